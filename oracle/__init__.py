@@ -1,0 +1,181 @@
+"""Oracle for the integer sort: TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library (``paper_cs_0004013_gb300``)
+never imports it and shares no code with it; when the CUDA library is missing
+the library fails instead of falling back to anything here.
+
+What the sort computes has a plain definition, so the oracle is that
+definition written out with numpy, with no blocking, fusion or reordering:
+
+* the sorted output is the keys in ascending unsigned order (Sec. 1.1: cell 0
+  holds the lowest values, cell 63 the highest);
+* with a payload, equal keys keep their input order: the method is a radix
+  sort whose low-order "sort" is retained while the higher digits are sorted
+  (Sec. 3.3.1), and the order inside a bucket must survive distribution (Sec. 5);
+* the output is split into ``P`` (= 64) equal contiguous partitions, the lower
+  partitions taking the extra element when P does not divide n (Sec. 1.1, and
+  the rule in footnote 7 of Sec. 3.4.2 that the lower cell gets the odd datum).
+
+The intermediate steps of the radix distribution are also given here, each as
+its definition, so that every kernel step can be checked on its own:
+
+* ``digit_histograms``: the count loop of the bucketing phase (Sec. 3.2) for
+  every digit at once;
+* ``digit_bases``: the cumulative bucket totals of Sec. 3.2, exclusive, i.e.
+  the number of keys whose digit is smaller (Sec. 4.4 orders it as
+  cumulative-then-sum, which gives the same numbers);
+* ``distribute``: one stable distribution by a digit, the "partial sort" of
+  Sec. 3.2 (grouped by bucket, buckets ascending) that keeps the earlier order
+  (Sec. 3.3.1);
+* ``skippable_digits``: a digit on which every key agrees moves nothing; the
+  paper's 30-bit observation (Sec. 4.5) is the case of the top digit.
+
+Pins against things other than itself live in ``tests/test_oracle.py``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "sort_keys",
+    "sort_pairs",
+    "partition_offsets",
+    "sort_segmented",
+    "digit_plan",
+    "digit_of",
+    "digit_histograms",
+    "digit_bases",
+    "skippable_digits",
+    "distribute",
+    "lsd_sort",
+    "msd_buckets",
+]
+
+
+def _u32(a) -> np.ndarray:
+    a = np.asarray(a)
+    if a.dtype != np.uint32:
+        a = a.astype(np.uint32)
+    return a
+
+
+def sort_keys(keys) -> np.ndarray:
+    """Keys in ascending unsigned 32-bit order (Sec. 1.1)."""
+    return np.sort(_u32(keys), kind="stable")
+
+
+def sort_pairs(keys, vals) -> tuple[np.ndarray, np.ndarray]:
+    """(key, value) pairs ordered by key alone; equal keys keep input order
+    (Sec. 3.3.1, Sec. 5)."""
+    keys = _u32(keys)
+    vals = _u32(vals)
+    if keys.shape != vals.shape:
+        raise ValueError("keys and vals differ in length")
+    perm = np.argsort(keys, kind="stable")
+    return keys[perm], vals[perm]
+
+
+def partition_offsets(n: int, num_parts: int = 64) -> np.ndarray:
+    """Start of each of ``num_parts`` equal contiguous output partitions and
+    the end n: partition p holds floor(n/P) elements, plus one when
+    p < n mod P (Sec. 1.1; footnote 7 of Sec. 3.4.2).  Returns uint64[P+1]."""
+    if num_parts < 1:
+        raise ValueError("num_parts must be >= 1")
+    q, r = divmod(int(n), int(num_parts))
+    p = np.arange(num_parts + 1, dtype=np.uint64)
+    return p * np.uint64(q) + np.minimum(p, np.uint64(r))
+
+
+def sort_segmented(keys, vals, seg_offsets, num_parts: int = 64):
+    """Each segment [seg_offsets[s], seg_offsets[s+1]) sorted on its own
+    (stable by key when ``vals`` is given), with the segment's partition
+    offsets made absolute by adding the segment start.  Returns
+    (keys_out, vals_out or None, part_offsets uint64[num_segs, P+1])."""
+    keys = _u32(keys)
+    seg_offsets = np.asarray(seg_offsets, dtype=np.uint64)
+    nseg = seg_offsets.size - 1
+    ko = np.empty_like(keys)
+    vo = None if vals is None else np.empty_like(_u32(vals))
+    po = np.zeros((max(nseg, 0), num_parts + 1), dtype=np.uint64)
+    for s in range(nseg):
+        a, b = int(seg_offsets[s]), int(seg_offsets[s + 1])
+        if vals is None:
+            ko[a:b] = sort_keys(keys[a:b])
+        else:
+            ko[a:b], vo[a:b] = sort_pairs(keys[a:b], _u32(vals)[a:b])
+        po[s] = partition_offsets(b - a, num_parts) + np.uint64(a)
+    return ko, vo, po
+
+
+def digit_plan(digit_bits: int, key_bits: int = 32) -> list[tuple[int, int]]:
+    """(shift, width) of each digit, least significant first; the last digit
+    takes what is left of the key (the paper's global radix splits 31 bits as
+    16 + 15, Sec. 5)."""
+    out, shift = [], 0
+    while shift < key_bits:
+        w = min(digit_bits, key_bits - shift)
+        out.append((shift, w))
+        shift += w
+    return out
+
+
+def digit_of(keys, shift: int, width: int) -> np.ndarray:
+    """The bucket index of each key: ``width`` bits starting at ``shift``
+    (Sec. 3.2 takes the top log2(buckets) bits with bit operations)."""
+    keys = _u32(keys).astype(np.uint64)
+    return ((keys >> np.uint64(shift)) & np.uint64((1 << width) - 1)).astype(np.int64)
+
+
+def digit_histograms(keys, plan: list[tuple[int, int]]) -> list[np.ndarray]:
+    """For every digit of ``plan``, how many keys fall in each of its 2^width
+    buckets (the count loop of Sec. 3.2).  Returns uint64 arrays."""
+    return [np.bincount(digit_of(keys, s, w), minlength=1 << w).astype(np.uint64)
+            for s, w in plan]
+
+
+def digit_bases(hist) -> np.ndarray:
+    """Exclusive cumulative totals: base[v] = number of keys whose digit is
+    below v, i.e. where bucket v starts in the distributed output (Sec. 3.2,
+    Sec. 4.4)."""
+    hist = np.asarray(hist, dtype=np.uint64)
+    base = np.zeros_like(hist)
+    if hist.size > 1:
+        base[1:] = np.cumsum(hist[:-1], dtype=np.uint64)
+    return base
+
+
+def skippable_digits(hists, n: int) -> list[bool]:
+    """A digit is skippable when one bucket holds all n keys: distributing by
+    it leaves every key where it is."""
+    return [bool(n > 0 and int(h.max()) == n) or n == 0 for h in hists]
+
+
+def distribute(keys, vals, shift: int, width: int):
+    """One stable distribution pass by a digit: keys grouped by bucket, buckets
+    in ascending order, input order kept inside a bucket (Sec. 3.2 partial
+    sort; Sec. 3.3.1).  ``vals`` may be None."""
+    keys = _u32(keys)
+    perm = np.argsort(digit_of(keys, shift, width), kind="stable")
+    return keys[perm], (None if vals is None else _u32(vals)[perm])
+
+
+def lsd_sort(keys, vals, digit_bits: int):
+    """The LSD radix sort of Sec. 3.3.1 spelled out: ``distribute`` by each
+    digit, least significant first.  Used only to pin ``distribute``; the
+    final result is checked against ``sort_keys``/``sort_pairs``."""
+    k, v = _u32(keys), (None if vals is None else _u32(vals))
+    for s, w in digit_plan(digit_bits):
+        k, v = distribute(k, v, s, w)
+    return k, v
+
+
+def msd_buckets(keys, vals, shift: int, width: int):
+    """The bucketing phase of Sec. 3.2 on the top digit: the stable
+    distribution by that digit plus where each bucket starts and ends.
+    Returns (keys, vals, bucket_offsets uint64[2^width + 1])."""
+    k, v = distribute(keys, vals, shift, width)
+    h = digit_histograms(keys, [(shift, width)])[0]
+    offs = np.zeros(h.size + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum(h, dtype=np.uint64)
+    return k, v, offs

@@ -1,0 +1,338 @@
+"""Pins of the oracle against things other than itself.
+
+The oracle (``oracle/``) is the definition of the sort written with numpy.
+These tests tie it to independent facts:
+
+* brute force: a hand-written stable insertion sort (pure Python) on small
+  inputs, and every input of length <= 6 over {0, 1, 2, 2^32-1};
+* invariants that together characterise a stable sort: ascending unsigned
+  order, the same multiset of keys (per-value counts), payloads of equal keys
+  increasing when the payload is the input position;
+* the partition rule of Sec. 1.1 / footnote 7 of Sec. 3.4.2: sizes sum to n,
+  differ by at most one, and never increase with the partition index, which
+  fixes the offsets uniquely; plus hand-worked fixtures under tests/golden/;
+* the radix steps of Sec. 3.2 / 3.3.1 against a hand-worked example and
+  against brute-force counting and bucket lists, and the LSD theorem (all
+  digits distributed low to high give the sorted order);
+* planted mistakes: mutated copies of oracle functions must fail the pins.
+"""
+from __future__ import annotations
+
+import itertools
+import os
+from collections import Counter
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U32MAX = (1 << 32) - 1
+
+
+# ---------------------------------------------------------------- brute force
+def insertion_sort_pairs(keys, vals):
+    """Stable insertion sort on Python ints: an element moves left only past
+    strictly greater keys."""
+    a = [(int(k), int(v)) for k, v in zip(keys, vals)]
+    for i in range(1, len(a)):
+        x = a[i]
+        j = i - 1
+        while j >= 0 and a[j][0] > x[0]:
+            a[j + 1] = a[j]
+            j -= 1
+        a[j + 1] = x
+    return [k for k, _ in a], [v for _, v in a]
+
+
+def brute_histogram(keys, shift, width):
+    """The count loop of Sec. 3.2, one element at a time."""
+    counts = [0] * (1 << width)
+    for k in keys:
+        counts[(int(k) >> shift) & ((1 << width) - 1)] += 1
+    return counts
+
+
+def brute_distribute(keys, vals, shift, width):
+    """Bucket lists: append each element to its bucket in input order, then
+    concatenate the buckets in ascending order."""
+    buckets = [[] for _ in range(1 << width)]
+    for k, v in zip(keys, vals):
+        buckets[(int(k) >> shift) & ((1 << width) - 1)].append((int(k), int(v)))
+    flat = [e for b in buckets for e in b]
+    return [k for k, _ in flat], [v for _, v in flat]
+
+
+# ------------------------------------------------------------------- checkers
+def check_sort_pairs(fn, keys):
+    """Raise AssertionError unless fn(keys, positions) is the stable sort."""
+    keys = np.asarray(keys, dtype=np.uint32)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    ko, vo = fn(keys, vals)
+    ko = [int(x) for x in ko]
+    vo = [int(x) for x in vo]
+    assert len(ko) == keys.size and len(vo) == keys.size
+    # ascending unsigned order
+    assert all(ko[i] <= ko[i + 1] for i in range(len(ko) - 1))
+    # same multiset of keys
+    assert Counter(ko) == Counter(int(x) for x in keys)
+    # every payload names the key it came with
+    assert all(int(keys[v]) == k for k, v in zip(ko, vo))
+    # stability: equal keys keep increasing input positions
+    assert all(vo[i] < vo[i + 1] for i in range(len(ko) - 1) if ko[i] == ko[i + 1])
+    bk, bv = insertion_sort_pairs(keys, vals)
+    assert ko == bk and vo == bv
+
+
+def check_offsets(fn, n, P):
+    off = [int(x) for x in fn(n, P)]
+    assert len(off) == P + 1 and off[0] == 0 and off[-1] == n
+    sizes = [off[i + 1] - off[i] for i in range(P)]
+    assert min(sizes) >= 0 and max(sizes) - min(sizes) <= 1
+    assert all(sizes[i] >= sizes[i + 1] for i in range(P - 1))
+
+
+def read_golden_offsets():
+    rows = []
+    with open(os.path.join(GOLDEN, "partition_offsets.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            head, tail = line.split("|")
+            n, P = (int(x) for x in head.split())
+            rows.append((n, P, [int(x) for x in tail.split()]))
+    return rows
+
+
+def read_golden_sorts():
+    rows = []
+    with open(os.path.join(GOLDEN, "sort_examples.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            fields = [[int(x) for x in part.split()] for part in line.split(";")]
+            rows.append(fields)
+    return rows
+
+
+def read_golden_radix():
+    d = {}
+    with open(os.path.join(GOLDEN, "radix_example.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, *vals = line.split()
+            d[name] = [int(x) for x in vals]
+    return d
+
+
+# ---------------------------------------------------------------------- tests
+def test_golden_sorts():
+    for keys, vals, sk, sv in read_golden_sorts():
+        ko, vo = oracle.sort_pairs(np.array(keys, np.uint32), np.array(vals, np.uint32))
+        assert list(ko) == sk and list(vo) == sv
+        assert list(oracle.sort_keys(np.array(keys, np.uint32))) == sk
+
+
+def test_golden_offsets():
+    rows = read_golden_offsets()
+    assert len(rows) >= 10
+    for n, P, want in rows:
+        assert [int(x) for x in oracle.partition_offsets(n, P)] == want, (n, P)
+
+
+def test_golden_radix_steps():
+    g = read_golden_radix()
+    keys = np.array(g["keys"], np.uint32)
+    vals = np.array(g["vals"], np.uint32)
+    h0, h1 = oracle.digit_histograms(keys, [(0, 2), (2, 2)])
+    assert list(h0) == g["hist0"] and list(h1) == g["hist1"]
+    assert list(oracle.digit_bases(h0)) == g["base0"]
+    assert list(oracle.digit_bases(h1)) == g["base1"]
+    k0, v0 = oracle.distribute(keys, vals, 0, 2)
+    assert list(k0) == g["pass0_keys"] and list(v0) == g["pass0_vals"]
+    k1, v1 = oracle.distribute(k0, v0, 2, 2)
+    assert list(k1) == g["pass1_keys"] and list(v1) == g["pass1_vals"]
+
+
+def test_exhaustive_tiny():
+    alphabet = [0, 1, 2, U32MAX]
+    count = 0
+    for n in range(0, 7):
+        for tup in itertools.product(alphabet, repeat=n):
+            check_sort_pairs(oracle.sort_pairs, tup)
+            count += 1
+    assert count == sum(4 ** n for n in range(7))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "few", "equal", "sorted", "reverse", "two", "topbit"])
+def test_bruteforce_small(dist):
+    rng_keys = synth.uniform31(2048, 1234).astype(np.uint64)
+    n = 2048 if dist != "uniform" else 1500
+    if dist == "uniform":
+        keys = rng_keys[:n] | (rng_keys[:n] << np.uint64(1)) & np.uint64(U32MAX)
+    elif dist == "few":
+        keys = rng_keys % np.uint64(7)
+    elif dist == "equal":
+        keys = np.full(n, 123456789, np.uint64)
+    elif dist == "sorted":
+        keys = np.sort(rng_keys)
+    elif dist == "reverse":
+        keys = np.sort(rng_keys)[::-1]
+    elif dist == "two":
+        keys = np.where(rng_keys & np.uint64(1), np.uint64(U32MAX), np.uint64(0))
+    else:  # values straddling 2^31: catches a signed comparison
+        keys = (np.uint64(1 << 31) - np.uint64(1024)) + rng_keys % np.uint64(2048)
+    check_sort_pairs(oracle.sort_pairs, keys.astype(np.uint32))
+    ko = oracle.sort_keys(keys.astype(np.uint32))
+    bk, _ = insertion_sort_pairs(keys, range(keys.size))
+    assert [int(x) for x in ko] == bk
+
+
+@pytest.mark.parametrize("name", sorted(synth.DISTRIBUTIONS))
+def test_invariants_each_distribution(name):
+    keys = synth.DISTRIBUTIONS[name](1 << 15, 99)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    ko, vo = oracle.sort_pairs(keys, vals)
+    assert np.all(ko[:-1] <= ko[1:])
+    assert np.array_equal(keys[vo], ko)
+    assert np.array_equal(np.sort(vo), vals)  # vals is a permutation
+    eq = ko[:-1] == ko[1:]
+    assert np.all(vo[:-1][eq] < vo[1:][eq])
+    assert Counter(ko.tolist()) == Counter(keys.tolist())
+
+
+@pytest.mark.parametrize("P", [1, 2, 3, 7, 63, 64, 65, 1000])
+def test_offsets_invariants(P):
+    for n in list(range(0, 3 * P + 3)) + [1 << 20, (1 << 26) + 7, (1 << 32) - 1]:
+        check_offsets(oracle.partition_offsets, n, P)
+
+
+def test_histograms_and_bases_bruteforce():
+    keys = synth.uniform31(4000, 7).astype(np.uint32) | np.uint32(1 << 31)
+    for plan in (oracle.digit_plan(8), oracle.digit_plan(11), [(5, 3), (0, 1)]):
+        hs = oracle.digit_histograms(keys, plan)
+        for (s, w), h in zip(plan, hs):
+            assert [int(x) for x in h] == brute_histogram(keys, s, w)
+            assert int(h.sum()) == keys.size
+            b = oracle.digit_bases(h)
+            dig = [(int(k) >> s) & ((1 << w) - 1) for k in keys]
+            cnt = Counter(dig)
+            # base[v] = number of keys whose digit is below v
+            running = 0
+            for v in range(1 << w):
+                assert int(b[v]) == running
+                running += cnt.get(v, 0)
+
+
+def test_digit_plan():
+    assert oracle.digit_plan(8) == [(0, 8), (8, 8), (16, 8), (24, 8)]
+    assert oracle.digit_plan(11) == [(0, 11), (11, 11), (22, 10)]
+    assert oracle.digit_plan(16, 31) == [(0, 16), (16, 15)]  # the 16+15 of Sec. 5
+
+
+def test_distribute_bruteforce_and_lsd_theorem():
+    keys = synth.gauss_mix(3000, 5)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    for s, w in [(0, 8), (8, 8), (22, 10), (0, 11), (3, 5)]:
+        k, v = oracle.distribute(keys, vals, s, w)
+        bk, bv = brute_distribute(keys, vals, s, w)
+        assert [int(x) for x in k] == bk and [int(x) for x in v] == bv
+    sk, sv = oracle.sort_pairs(keys, vals)
+    for bits in (1, 4, 8, 11, 13, 16):
+        k, v = oracle.lsd_sort(keys, vals, bits)
+        assert np.array_equal(k, sk) and np.array_equal(v, sv), bits
+
+
+def test_msd_buckets_then_local_sort():
+    keys = synth.tight_clusters(5000, 3)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    k, v, offs = oracle.msd_buckets(keys, vals, 21, 11)
+    assert int(offs[0]) == 0 and int(offs[-1]) == keys.size
+    # sorting each bucket on its own gives the full stable sort
+    outk, outv = k.copy(), v.copy()
+    for b in range(offs.size - 1):
+        a, e = int(offs[b]), int(offs[b + 1])
+        outk[a:e], outv[a:e] = oracle.sort_pairs(k[a:e], v[a:e])
+    sk, sv = oracle.sort_pairs(keys, vals)
+    assert np.array_equal(outk, sk) and np.array_equal(outv, sv)
+
+
+def test_skippable_digits():
+    keys = (synth.uniform31(1000, 1) & np.uint32(0x3FF)) | np.uint32(0x5 << 24)
+    plan = oracle.digit_plan(8)
+    sk = oracle.skippable_digits(oracle.digit_histograms(keys, plan), keys.size)
+    assert sk == [False, False, True, True]
+    for (s, w), skip in zip(plan, sk):
+        if skip:  # distributing by a skippable digit moves nothing
+            k, _ = oracle.distribute(keys, None, s, w)
+            assert np.array_equal(k, keys)
+
+
+def test_segmented_bruteforce():
+    sizes = [0, 1, 5, 0, 40, 3, 0]
+    offs = np.zeros(len(sizes) + 1, np.uint64)
+    offs[1:] = np.cumsum(sizes)
+    n = int(offs[-1])
+    keys = (synth.uniform31(n, 17) % np.uint32(9)).astype(np.uint32)
+    vals = np.arange(n, dtype=np.uint32)
+    ko, vo, po = oracle.sort_segmented(keys, vals, offs, num_parts=4)
+    for s in range(len(sizes)):
+        a, b = int(offs[s]), int(offs[s + 1])
+        bk, bv = insertion_sort_pairs(keys[a:b], vals[a:b])
+        assert [int(x) for x in ko[a:b]] == bk and [int(x) for x in vo[a:b]] == bv
+        assert int(po[s, 0]) == a and int(po[s, -1]) == b
+        check_offsets(lambda m, P: po[s] - np.uint64(a), b - a, 4)
+    ko2, vo2, _ = oracle.sort_segmented(keys, None, offs, num_parts=4)
+    assert vo2 is None and np.array_equal(ko2, ko)
+
+
+# ------------------------------------------------------------ planted mistakes
+def _mut_signed(keys, vals):
+    perm = np.argsort(keys.astype(np.int32), kind="stable")
+    return keys[perm], vals[perm]
+
+
+def _mut_unstable(keys, vals):
+    # reverse the input, then stable sort: equal keys come out reversed
+    r = keys[::-1]
+    perm = np.argsort(r, kind="stable")
+    return r[perm], vals[::-1][perm]
+
+
+def _mut_drop(keys, vals):
+    k, v = oracle.sort_pairs(keys, vals)
+    if k.size:
+        k, v = k.copy(), v.copy()
+        k[-1], v[-1] = k[0], v[0]
+    return k, v
+
+
+def _mut_offsets_upper(n, P):
+    q, r = divmod(n, P)
+    sizes = [q + (1 if p >= P - r else 0) for p in range(P)]
+    return np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+
+
+def _mut_bases_inclusive(h):
+    return np.cumsum(np.asarray(h, np.uint64))
+
+
+@pytest.mark.parametrize("mut", [_mut_signed, _mut_unstable, _mut_drop])
+def test_planted_sort_mistakes_are_caught(mut):
+    caught = False
+    for keys in ([U32MAX, 0, 1 << 31, 5], [2, 1, 2, 1, 2], [3, 1, 2, 1]):
+        try:
+            check_sort_pairs(mut, keys)
+        except AssertionError:
+            caught = True
+    assert caught
+
+
+def test_planted_offset_and_base_mistakes_are_caught():
+    with pytest.raises(AssertionError):
+        check_offsets(_mut_offsets_upper, 10, 4)
+    h = oracle.digit_histograms(np.array([13, 6, 9, 2, 14, 5], np.uint32), [(0, 2)])[0]
+    assert list(_mut_bases_inclusive(h)) != read_golden_radix()["base0"]
