@@ -1,0 +1,343 @@
+"""Throughput of the GB300 radix sort: Gkeys/s sorting 2^26 uint32 keys.
+
+One step = one whole sort (upfront histogram, digit scans, every onesweep
+pass) of 2^26 uniform 31-bit keys already resident in HBM, keys only, with
+the 64 partition offsets.  The keys (268 MB) exceed the 126 MB L2, so no
+flush is needed between steps.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the oracle (a plain numpy sort, one host core) on a
+bounded sample of the same workload.  Under torchrun every rank sorts its
+own 2^26 keys (replicas: the sort does not shard across GPUs here); the
+value is all ranks' keys over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s sorting 2^26 u32 on 1 GB300, % HBM roofline; batched/served vs plain"
+N_KEYS = 1 << 26
+WORKLOAD = "plain sort of 2^26 uint32 keys uniform in [0, 2^31-1], keys only, 64 partitions"
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 126 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_KEYS, help="keys per sort (default 2^26)")
+    ap.add_argument("--digit-bits", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--pairs", action="store_true", help="time key+payload sorts as the main value")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ cpu baseline
+def cpu_baseline(sample_keys: int = 1 << 22, budget_s: float = 12.0):
+    """The oracle as it stands (numpy stable sort, one core) on a bounded
+    sample of the workload: repeated sorts of 2^22 uniform keys."""
+    import oracle
+    import synth
+    keys = synth.uniform31(sample_keys, synth.CONFIG_SEED + 2)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.sort_keys(keys)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or reps >= 50:
+            break
+    rate = reps * sample_keys / el / 1e9
+    return {"value": rate, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} sorts of 2^22 uniform 31-bit keys (numpy stable sort), {el:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    keys = synth.uniform31(1 << 22, synth.CONFIG_SEED + 2)
+    for _ in range(args.warmup):
+        oracle.sort_keys(keys)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sort_keys(keys)
+        t.append(time.perf_counter() - t0)
+    tot = sum(t)
+    rate = args.steps * keys.size / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "Gkeys/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_keys_per_step": int(keys.size)},
+            "cpu_baseline": {"value": rate, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step sorts 2^22 of the workload's uniform 31-bit keys "
+                                       "(numpy stable sort, one host core)"},
+            "e2e": {"value": rate, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours
+def traffic_from_profiles(kernel_file: str, key: str):
+    """DRAM bytes per launch recorded by ncu for the pass kernel, valid only
+    while the kernel source is unchanged (its sha256 is stored with it)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_cs_0004013_gb300", "csrc", kernel_file)
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            f = line.split()
+            if len(f) >= 3 and f[0] == key and f[1] == sha:
+                return float(f[2])
+    except OSError:
+        pass
+    return None
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import synth
+    import paper_cs_0004013_gb300 as rs
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = args.n
+    keys = synth.uniform31(n, synth.CONFIG_SEED + 2 + 1000 * rank)
+    d_keys = torch.from_numpy(keys.view(np.int32)).to(dev)
+    d_out = torch.empty_like(d_keys)
+    plan = {"digit_bits": args.digit_bits, "tile": args.tile}
+    pairs = args.pairs
+    if pairs:
+        d_vals = torch.arange(n, dtype=torch.int32, device=dev)
+        d_vout = torch.empty_like(d_vals)
+        temp = torch.empty(rs.rs_sort_u32_pairs(None, None, None, None, n, plan=plan), dtype=torch.uint8,
+                           device=dev)
+    else:
+        temp = torch.empty(rs.rs_sort_u32(None, None, n, plan=plan), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        if pairs:
+            rs.rs_sort_u32_pairs(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
+        else:
+            rs.rs_sort_u32(d_keys, d_out, n, 64, plan, temp, stream, want_offsets=True)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    rs.rs_trace_read()  # drop warm-up records
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rs.rs_trace_enable(True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    rs.rs_trace_enable(False)
+    rs.rs_check_device_error()
+    trace = rs.rs_trace_read()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n * args.steps / (ms * 1e-3) / 1e9
+
+    # bytes of the executed plan: one read for the histograms, then a read
+    # and a write per pass (keys; plus payload for pairs)
+    pass_kind = None
+    for k in ("onesweep_r11", "onesweep_r8"):
+        if k in trace:
+            pass_kind = k
+    passes = trace[pass_kind]["launches"] // args.steps if pass_kind else 0
+    bpk = 4 + passes * (16 if pairs else 8)
+    peak, peak_kind = measured_peak()
+    roof = None
+    if pass_kind:
+        tr = trace[pass_kind]
+        avg_ms = tr["total_ms"] / tr["launches"]
+        bytes_launch = (16 if pairs else 8) * tr["keys"] / tr["launches"]
+        achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
+        key = f"{pass_kind}_{'pairs' if pairs else 'keys'}_n{n}"
+        traffic = traffic_from_profiles("onesweep.cuh", key)
+        roof = {"bound": "hbm", "kernel": pass_kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms}
+    launches = sum(v["launches"] for k, v in trace.items() if k != "clear")
+
+    # end to end through the same API: pinned host keys in, sorted keys out
+    e2e = None
+    if not args.no_e2e and not pairs:
+        h_in = torch.from_numpy(keys.view(np.int32)).pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        d_in2 = torch.empty_like(d_keys)
+
+        def e2e_step():
+            d_in2.copy_(h_in, non_blocking=True)
+            rs.rs_sort_u32(d_in2, d_out, n, 64, plan, temp, stream, want_offsets=True)
+            h_out.copy_(d_out, non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ems], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * n * args.steps / (ems * 1e-3) / 1e9, "unit": "Gkeys/s",
+               "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
+        ok = np.array_equal(h_out.numpy().view(np.uint32)[:: max(1, n // 4096)],
+                            np.sort(keys)[:: max(1, n // 4096)])
+        if not ok:
+            raise SystemExit("end-to-end output is not the sorted keys")
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD if not pairs else WORKLOAD.replace("keys only", "key+payload"),
+                       "n": n, "digit_bits": args.digit_bits or "auto", "passes": passes,
+                       "algorithmic_bytes_per_key": bpk,
+                       "sort_roofline_frac": value / world * 1e9 * bpk / (peak * 1e9),
+                       "l2": f"inputs ({4 * n / 1e6:.0f} MB) exceed L2 ({L2_BYTES / 1e6:.0f} MB); no flush",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "kernel_ms": {k: v["total_ms"] / max(v["launches"], 1) for k, v in trace.items()},
+            "clocks": clocks.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

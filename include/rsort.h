@@ -1,0 +1,176 @@
+/*
+ * rsort.h: C ABI of librsort, a GB300 (sm_103a) radix distribution sort of
+ * 32-bit unsigned keys, after Weaver & Lynes, "Sorting Integers on the
+ * AP1000" (1994).
+ *
+ * What is computed (the paper's contract and method):
+ *  - Sec. 1.1: the keys end up in ascending order, split evenly into
+ *    num_parts (the contest used 64) contiguous partitions, partition 0
+ *    holding the lowest values.  When num_parts does not divide n the lower
+ *    partitions take the extra element (footnote 7 of Sec. 3.4.2), so
+ *    partition p starts at  off[p] = p * floor(n / P) + min(p, n mod P).
+ *  - Sec. 3.2 / 3.3.1 / 5: the sort is a radix distribution: per digit, a
+ *    histogram of the digit ("increment bucket"), its cumulative totals,
+ *    and a stable "partial sort" that groups keys by bucket in ascending
+ *    bucket order, repeated from the low digit to the high one with the
+ *    earlier order kept.  Pairs are therefore sorted STABLY by key.
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers ("d_" or unprefixed key/value buffers) must be device
+ *    memory of the current CUDA device, 4-byte aligned.  Host pointers are
+ *    prefixed "h_".
+ *  - The caller owns all memory.  The library never allocates: scratch comes
+ *    in through (temp, temp_bytes).  Passing temp == NULL is a size query:
+ *    *temp_bytes is set to the bytes needed and RS_OK is returned, nothing
+ *    else happens.  temp must be 256-byte aligned.  The size needed depends
+ *    only on the entry point, n (or total_n), the payload flag and the plan.
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default) and
+ *    is asynchronous: a return of RS_OK means the arguments were valid and
+ *    the launches were enqueued.  Errors raised on the device (a bounded
+ *    wait that gave up) are reported by rs_check_device_error().
+ *  - Inputs are never modified; outputs must not overlap inputs or temp
+ *    (RS_ERR_INVALID).  n = 0 is valid.  n must be below 2^32.
+ *  - On any error the thread-local message of rs_last_error() says why.
+ */
+#ifndef RSORT_H
+#define RSORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, so callers need no CUDA header. */
+typedef struct CUstream_st* rs_stream_t;
+
+typedef enum rs_status {
+  RS_OK = 0,
+  RS_ERR_INVALID = 1,        /* bad pointer, size, alignment or overlap */
+  RS_ERR_TEMP_TOO_SMALL = 2, /* *temp_bytes below the queried size */
+  RS_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  RS_ERR_TIMEOUT = 4,        /* a device-side bounded wait gave up */
+  RS_ERR_UNSUPPORTED = 5     /* a plan field this build does not offer */
+} rs_status;
+
+/* Radix plan.  Zero fields mean "choose automatically" (the autotuner's
+ * table, keyed by n and the payload flag).
+ *   digit_bits: 8 (four passes over 32-bit keys) or 11 (three passes,
+ *               11 + 11 + 10 bits).  The paper's bucketing used 12-13 bit
+ *               buckets (Sec. 3.2, Sec. 4.7) and planned a 16 + 15-bit
+ *               global radix (Sec. 5).
+ *   mode:       RS_MODE_LSD = least significant digit first (Sec. 3.3.1);
+ *               RS_MODE_MSD = bucket by the top digit first, then sort each
+ *               bucket locally (the bucketing + local sort pipeline of
+ *               Sec. 3 / Sec. 4.6).
+ *   tile:       index of the kernel tile shape (0 = automatic).            */
+enum { RS_MODE_AUTO = 0, RS_MODE_LSD = 1, RS_MODE_MSD = 2 };
+typedef struct rs_plan {
+  uint32_t digit_bits;
+  uint32_t mode;
+  uint32_t tile;
+  uint32_t reserved;
+} rs_plan;
+
+/* Sort n keys ascending into keys_out and write the num_parts + 1 partition
+ * offsets (Sec. 1.1, footnote 7) to the HOST array h_part_offsets (may be
+ * NULL if not wanted).  num_parts >= 1.  plan may be NULL (automatic).      */
+rs_status rs_sort_u32(const uint32_t* keys_in, uint32_t* keys_out, uint64_t n,
+                      uint32_t num_parts, uint64_t* h_part_offsets,
+                      const rs_plan* plan, void* temp, size_t* temp_bytes,
+                      rs_stream_t stream);
+
+/* Stable sort of (key, value) pairs by key (Sec. 3.3.1: the earlier digits'
+ * order is kept; Sec. 5: the order inside a bucket survives distribution).
+ * Equal keys keep their input order.  Otherwise as rs_sort_u32.             */
+rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in,
+                            uint32_t* keys_out, uint32_t* vals_out, uint64_t n,
+                            uint32_t num_parts, uint64_t* h_part_offsets,
+                            const rs_plan* plan, void* temp, size_t* temp_bytes,
+                            rs_stream_t stream);
+
+/* Many independent sorts in one call.  Segment s is
+ * [d_seg_offsets[s], d_seg_offsets[s+1]) of the concatenated arrays
+ * (DEVICE array of num_segs + 1 uint64, non-decreasing, last = total_n).
+ * Each segment is sorted on its own (stably when vals_in != NULL; with
+ * vals_in == NULL, vals_out must be NULL too).  d_part_offsets (DEVICE,
+ * num_segs * (num_parts + 1) uint64, may be NULL) receives each segment's
+ * partition offsets made absolute by adding the segment start.
+ * h_seg_offsets is a HOST copy of the same offsets, used to plan the
+ * launches (segment classes by size) without reading device memory.        */
+rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in,
+                                uint32_t* keys_out, uint32_t* vals_out,
+                                const uint64_t* d_seg_offsets,
+                                const uint64_t* h_seg_offsets, uint32_t num_segs,
+                                uint64_t total_n, uint32_t num_parts,
+                                uint64_t* d_part_offsets, const rs_plan* plan,
+                                void* temp, size_t* temp_bytes, rs_stream_t stream);
+
+/* ---- single steps of the method, for step-by-step checking ------------- */
+
+/* The count loop of Sec. 3.2 for every digit of a digit_bits-wide plan in
+ * one read of the keys, plus the exclusive cumulative totals (Sec. 3.2,
+ * Sec. 4.4).  With D = ceil(32 / digit_bits) digits and B = 2^digit_bits:
+ *   d_hist [D][B] (DEVICE uint32): keys per bucket of each digit;
+ *   d_bases[D][B] (DEVICE uint32, may be NULL): keys with a smaller digit;
+ *   d_skip [D]    (DEVICE uint32, may be NULL): 1 when one bucket of that
+ *                 digit holds all n keys (the pass would move nothing).
+ * Digit j covers bits [j * digit_bits, min(32, (j + 1) * digit_bits)).
+ * digit_bits must be 8 or 11.  Needs no temp.                               */
+rs_status rs_digit_histograms(const uint32_t* keys, uint64_t n, uint32_t digit_bits,
+                              uint32_t* d_hist, uint32_t* d_bases, uint32_t* d_skip,
+                              rs_stream_t stream);
+
+/* One stable distribution of (keys, vals) by the digit of `width` bits at
+ * `shift` (the "partial sort" of Sec. 3.2; one pass of Sec. 3.3.1):
+ * keys grouped by digit value, in ascending order, input order kept within
+ * a digit value.  vals_in/vals_out may both be NULL.  width must be 1..11
+ * and shift + width <= 32.  Temp as for the sorts.                          */
+rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in,
+                        uint32_t* keys_out, uint32_t* vals_out, uint64_t n,
+                        uint32_t shift, uint32_t width, void* temp,
+                        size_t* temp_bytes, rs_stream_t stream);
+
+/* ---- errors ------------------------------------------------------------- */
+
+/* Message for the last error raised on the calling thread ("" if none). */
+const char* rs_last_error(void);
+
+/* Waits for `stream`, then reports and clears the device error word of the
+ * current device: RS_ERR_TIMEOUT if a kernel's bounded wait (the
+ * cross-tile lookback) gave up since the last check; RS_ERR_CUDA if the
+ * stream failed or a kernel's output-index check fired (the write was
+ * skipped); else RS_OK.  The error word is shared by all streams of the
+ * device.                                                                   */
+rs_status rs_check_device_error(rs_stream_t stream);
+
+/* ---- tracing ------------------------------------------------------------ */
+
+/* Per-kernel timing.  While enabled, every kernel the library launches is
+ * bracketed by two CUDA events recorded on the launch's stream (the events
+ * are created on first use and kept for reuse; enabling costs two event
+ * records per launch and no synchronisation).                              */
+typedef struct rs_trace_entry {
+  char name[32];      /* kernel kind: "upfront_hist", "digit_scan",
+                         "onesweep_r8", "onesweep_r11", "clear", ...        */
+  uint32_t launches;  /* launches of this kind since the last read         */
+  uint32_t reserved;
+  double total_ms;    /* sum of their event-to-event times                 */
+  double keys;        /* sum of the keys each launch processed             */
+} rs_trace_entry;
+
+rs_status rs_trace_enable(int on);
+
+/* Waits for every traced launch, writes up to `capacity` entries (one per
+ * kernel kind seen) and resets the trace.  *count = entries written.       */
+rs_status rs_trace_read(rs_trace_entry* out, uint32_t capacity, uint32_t* count);
+
+/* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
+uint32_t rs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSORT_H */

@@ -1,0 +1,266 @@
+"""Python binding of librsort: a GB300 radix distribution sort of uint32 keys.
+
+Argument marshalling only: every step of the sort runs in the CUDA kernels
+of ``librsort.so`` (built in-tree by ``build.py``).  The functions named
+``rs_*`` mirror the C entry points of ``include/rsort.h`` one to one and take
+torch CUDA tensors (int32 or uint32; only their device pointers are used).
+``sort``, ``sort_pairs`` and ``sort_segmented`` are conveniences that also
+allocate the outputs and the temp buffer through torch.
+
+There is no fallback: if the library is missing or fails to load, importing
+this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB as LIBRARY_PATH
+
+__all__ = [
+    "RsError", "RsPlan", "lib", "LIBRARY_PATH",
+    "rs_sort_u32", "rs_sort_u32_pairs", "rs_sort_u32_segmented", "rs_digit_histograms",
+    "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_version", "rs_trace_enable",
+    "rs_trace_read",
+    "sort", "sort_pairs", "sort_segmented", "temp_bytes", "part_offsets",
+    "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD",
+]
+
+STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_TEMP_TOO_SMALL", 3: "RS_ERR_CUDA",
+                4: "RS_ERR_TIMEOUT", 5: "RS_ERR_UNSUPPORTED"}
+RS_MODE_AUTO, RS_MODE_LSD, RS_MODE_MSD = 0, 1, 2
+
+
+class RsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class RsTraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("total_ms", ctypes.c_double), ("keys", ctypes.c_double)]
+
+
+class RsPlan(ctypes.Structure):
+    _fields_ = [("digit_bits", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("tile", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_P = ctypes.c_void_p
+_U32 = ctypes.c_uint32
+_U64 = ctypes.c_uint64
+_SZP = ctypes.POINTER(ctypes.c_size_t)
+_U64P = ctypes.POINTER(ctypes.c_uint64)
+_PLANP = ctypes.POINTER(RsPlan)
+
+_SIGS = {
+    "rs_sort_u32": [_P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
+    "rs_sort_u32_pairs": [_P, _P, _P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
+    "rs_sort_u32_segmented": [_P, _P, _P, _P, _P, _U64P, _U32, _U64, _U32, _P, _PLANP, _P, _SZP, _P],
+    "rs_digit_histograms": [_P, _U64, _U32, _P, _P, _P, _P],
+    "rs_radix_pass": [_P, _P, _P, _P, _U64, _U32, _U32, _P, _SZP, _P],
+    "rs_last_error": [],
+    "rs_check_device_error": [_P],
+    "rs_version": [],
+    "rs_trace_enable": [ctypes.c_int],
+    "rs_trace_read": [ctypes.POINTER(RsTraceEntry), _U32, ctypes.POINTER(ctypes.c_uint32)],
+}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIBRARY_PATH):
+        raise ImportError(f"{LIBRARY_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    # the CUDA runtime the library links against is the one torch loaded
+    import torch  # noqa: F401
+    dll = ctypes.CDLL(LIBRARY_PATH)
+    for name, args in _SIGS.items():
+        f = getattr(dll, name)
+        f.argtypes = args
+        f.restype = ctypes.c_char_p if name == "rs_last_error" else ctypes.c_int
+    return dll
+
+
+lib = _load()
+
+
+def rs_last_error() -> str:
+    return lib.rs_last_error().decode()
+
+
+def rs_version() -> int:
+    return int(lib.rs_version())
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise RsError(status, rs_last_error())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _plan(plan) -> ctypes.POINTER(RsPlan) | None:
+    if plan is None:
+        return None
+    if isinstance(plan, RsPlan):
+        return ctypes.pointer(plan)
+    return ctypes.pointer(RsPlan(int(plan.get("digit_bits", 0)), int(plan.get("mode", 0)),
+                                 int(plan.get("tile", 0)), 0))
+
+
+def _temp(temp):
+    if temp is None:
+        return None, ctypes.c_size_t(0)
+    return _ptr(temp), ctypes.c_size_t(temp.numel() * temp.element_size())
+
+
+# ------------------------------------------------------------- C entry points
+def rs_sort_u32(keys_in, keys_out, n: int, num_parts: int = 64, plan=None, temp=None,
+                stream=None, want_offsets: bool = True):
+    """Calls rs_sort_u32.  With temp=None it is the size query and returns
+    the bytes needed; otherwise it returns the partition offsets (numpy
+    uint64[num_parts + 1]) or None."""
+    tp, tb = _temp(temp)
+    offs = np.zeros(num_parts + 1, dtype=np.uint64) if (want_offsets and temp is not None) else None
+    op = offs.ctypes.data_as(_U64P) if offs is not None else None
+    _check(lib.rs_sort_u32(_ptr(keys_in), _ptr(keys_out), n, num_parts, op, _plan(plan), tp,
+                           ctypes.byref(tb), _stream(stream) if temp is not None else None))
+    return tb.value if temp is None else offs
+
+
+def rs_sort_u32_pairs(keys_in, vals_in, keys_out, vals_out, n: int, num_parts: int = 64, plan=None,
+                      temp=None, stream=None, want_offsets: bool = True):
+    """Calls rs_sort_u32_pairs; returns as rs_sort_u32."""
+    tp, tb = _temp(temp)
+    offs = np.zeros(num_parts + 1, dtype=np.uint64) if (want_offsets and temp is not None) else None
+    op = offs.ctypes.data_as(_U64P) if offs is not None else None
+    _check(lib.rs_sort_u32_pairs(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n, num_parts,
+                                 op, _plan(plan), tp, ctypes.byref(tb),
+                                 _stream(stream) if temp is not None else None))
+    return tb.value if temp is None else offs
+
+
+def rs_sort_u32_segmented(keys_in, vals_in, keys_out, vals_out, d_seg_offsets, h_seg_offsets,
+                          num_segs: int, total_n: int, num_parts: int = 64, d_part_offsets=None,
+                          plan=None, temp=None, stream=None):
+    """Calls rs_sort_u32_segmented (h_seg_offsets: numpy uint64[num_segs+1]).
+    With temp=None returns the bytes needed."""
+    tp, tb = _temp(temp)
+    h = np.ascontiguousarray(h_seg_offsets, dtype=np.uint64)
+    _check(lib.rs_sort_u32_segmented(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out),
+                                     _ptr(d_seg_offsets), h.ctypes.data_as(_U64P), num_segs, total_n,
+                                     num_parts, _ptr(d_part_offsets), _plan(plan), tp, ctypes.byref(tb),
+                                     _stream(stream) if temp is not None else None))
+    return tb.value if temp is None else None
+
+
+def rs_digit_histograms(keys, n: int, digit_bits: int, d_hist, d_bases=None, d_skip=None, stream=None):
+    _check(lib.rs_digit_histograms(_ptr(keys), n, digit_bits, _ptr(d_hist), _ptr(d_bases), _ptr(d_skip),
+                                   _stream(stream)))
+
+
+def rs_radix_pass(keys_in, vals_in, keys_out, vals_out, n: int, shift: int, width: int, temp=None,
+                  stream=None):
+    tp, tb = _temp(temp)
+    _check(lib.rs_radix_pass(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n, shift, width,
+                             tp, ctypes.byref(tb), _stream(stream) if temp is not None else None))
+    return tb.value if temp is None else None
+
+
+def rs_check_device_error(stream=None) -> None:
+    _check(lib.rs_check_device_error(_stream(stream)))
+
+
+def rs_trace_enable(on: bool = True) -> None:
+    _check(lib.rs_trace_enable(1 if on else 0))
+
+
+def rs_trace_read() -> dict:
+    """{kernel kind: {"launches", "total_ms", "keys"}} since the last read."""
+    buf = (RsTraceEntry * 32)()
+    cnt = ctypes.c_uint32(0)
+    _check(lib.rs_trace_read(buf, 32, ctypes.byref(cnt)))
+    return {buf[i].name.decode(): {"launches": int(buf[i].launches), "total_ms": float(buf[i].total_ms),
+                                   "keys": float(buf[i].keys)} for i in range(cnt.value)}
+
+
+# --------------------------------------------------------------- conveniences
+def part_offsets(n: int, num_parts: int = 64) -> np.ndarray:
+    """Host copy of the partition offsets formula (no device work)."""
+    q, r = divmod(n, num_parts)
+    return np.array([p * q + min(p, r) for p in range(num_parts + 1)], dtype=np.uint64)
+
+
+def _empty_u32(n, device):
+    import torch
+    return torch.empty(max(n, 0), dtype=torch.int32, device=device)
+
+
+def temp_bytes(n: int, pairs: bool = False, plan=None) -> int:
+    if pairs:
+        return rs_sort_u32_pairs(None, None, None, None, n, plan=plan)
+    return rs_sort_u32(None, None, n, plan=plan)
+
+
+def _alloc_temp(nbytes: int, device):
+    import torch
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def sort(keys, num_parts: int = 64, plan=None, out=None, temp=None, stream=None):
+    """Sorted copy of a CUDA tensor of uint32 keys (int32/uint32 storage) and
+    the host partition offsets."""
+    n = keys.numel()
+    out = _empty_u32(n, keys.device) if out is None else out
+    if temp is None:
+        temp = _alloc_temp(rs_sort_u32(None, None, n, plan=plan), keys.device)
+    offs = rs_sort_u32(keys, out, n, num_parts, plan, temp, stream)
+    return out, offs
+
+
+def sort_pairs(keys, vals, num_parts: int = 64, plan=None, out_keys=None, out_vals=None, temp=None,
+               stream=None):
+    n = keys.numel()
+    ko = _empty_u32(n, keys.device) if out_keys is None else out_keys
+    vo = _empty_u32(n, keys.device) if out_vals is None else out_vals
+    if temp is None:
+        temp = _alloc_temp(rs_sort_u32_pairs(None, None, None, None, n, plan=plan), keys.device)
+    offs = rs_sort_u32_pairs(keys, vals, ko, vo, n, num_parts, plan, temp, stream)
+    return ko, vo, offs
+
+
+def sort_segmented(keys, vals, seg_offsets_host, num_parts: int = 64, plan=None, temp=None, stream=None,
+                   want_part_offsets: bool = True):
+    """Segmented sort; seg_offsets_host is a numpy uint64 array (num_segs+1)."""
+    import torch
+    h = np.ascontiguousarray(seg_offsets_host, dtype=np.uint64)
+    num_segs = h.size - 1
+    total = int(h[-1]) if h.size else 0
+    dev = keys.device
+    d_seg = torch.from_numpy(h.view(np.int64)).to(dev)
+    ko = _empty_u32(total, dev)
+    vo = _empty_u32(total, dev) if vals is not None else None
+    po = torch.empty(num_segs * (num_parts + 1), dtype=torch.int64, device=dev) if want_part_offsets else None
+    if temp is None:
+        nb = rs_sort_u32_segmented(None, vals, None, vo, None, h, num_segs, total, num_parts, plan=plan)
+        temp = _alloc_temp(nb, dev)
+    rs_sort_u32_segmented(keys, vals, ko, vo, d_seg, h, num_segs, total, num_parts, po, plan, temp, stream)
+    return ko, vo, po

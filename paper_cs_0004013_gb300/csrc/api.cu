@@ -1,0 +1,591 @@
+// C ABI of librsort (declared in include/rsort.h): argument checks, the
+// radix plan, the layout of the caller's temp buffer and the launches.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rs_device.cuh"
+#include "rs_internal.h"
+#include "rsort.h"
+
+namespace rs {
+namespace {
+
+constexpr uint32_t kVersion = 1 * 10000 + 0 * 100 + 0;
+constexpr int kMaxDevices = 64;
+constexpr size_t kAlign = 256;
+
+thread_local std::string g_last_error;
+
+rs_status fail(rs_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+rs_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(RS_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define RS_CUDA(call, what)                   \
+  do {                                        \
+    cudaError_t e_ = (call);                  \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+// Device error word: set by kernels whose bounded waits gave up.
+__device__ uint32_t g_err_word;
+
+struct DeviceState {
+  bool ready = false;
+  uint32_t* err = nullptr;
+  int num_sms = 0;
+};
+std::mutex g_mu;
+DeviceState g_dev[kMaxDevices];
+
+rs_status device_state(DeviceState** out) {
+  int dev = 0;
+  RS_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(RS_ERR_UNSUPPORTED, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_mu);
+  DeviceState& st = g_dev[dev];
+  if (!st.ready) {
+    RS_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&st.err), g_err_word), "cudaGetSymbolAddress(error word)");
+    RS_CUDA(cudaDeviceGetAttribute(&st.num_sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    int cnt = 0;
+    for (int r : {8, 11}) {
+      const OnesweepKernel* ks = r == 8 ? onesweep_kernels_r8(&cnt) : onesweep_kernels_r11(&cnt);
+      for (int i = 0; i < cnt; ++i)
+        RS_CUDA(cudaFuncSetAttribute(ks[i].func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks[i].smem)),
+                "cudaFuncSetAttribute(onesweep)");
+      const HistKernel* h = hist_kernel(r);
+      RS_CUDA(cudaFuncSetAttribute(h->func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
+              "cudaFuncSetAttribute(hist)");
+    }
+    st.ready = true;
+  }
+  *out = &st;
+  return RS_OK;
+}
+
+// ---- tracing -------------------------------------------------------------------
+enum TraceKind { T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_KINDS };
+const char* const kTraceNames[T_KINDS] = {"clear", "upfront_hist", "digit_scan", "onesweep_r8", "onesweep_r11",
+                                          "seg_part_offsets"};
+struct TraceRec {
+  int kind;
+  double keys;
+  cudaEvent_t a, b;
+};
+std::mutex g_trace_mu;
+bool g_trace_on = false;
+std::vector<TraceRec> g_trace;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaError_t take_event(cudaEvent_t* e) {
+  if (!g_event_pool.empty()) {
+    *e = g_event_pool.back();
+    g_event_pool.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreate(e);
+}
+
+// Runs `launch` (which enqueues one kernel or memset on s), bracketed by
+// events when tracing is on.
+template <class F>
+cudaError_t traced(int kind, double keys, cudaStream_t s, F&& launch) {
+  std::unique_lock<std::mutex> lock(g_trace_mu);
+  if (!g_trace_on) {
+    lock.unlock();
+    return launch();
+  }
+  TraceRec r{kind, keys, nullptr, nullptr};
+  cudaError_t e = take_event(&r.a);
+  if (e == cudaSuccess) e = take_event(&r.b);
+  if (e == cudaSuccess) e = cudaEventRecord(r.a, s);
+  if (e != cudaSuccess) return e;
+  e = launch();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(r.b, s);
+  if (e == cudaSuccess) g_trace.push_back(r);
+  return e;
+}
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  if (!a || !b || na == 0 || nb == 0) return false;
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+// ---- plan -------------------------------------------------------------------
+struct SortPlan {
+  int R = 11;
+  int nd = 0;
+  DigitSpec dig[kMaxDigits] = {};
+  const OnesweepKernel* k = nullptr;
+  size_t num_tiles = 0;
+};
+
+int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 11; }
+
+// n + one tile must fit the 30-bit count field of 32-bit status words.
+bool needs_wide_status(uint64_t n) { return n + 65536 > uint64_t(StatusCodec<uint32_t>::kVal); }
+
+rs_status pick_kernel(int R, uint32_t tile_idx, bool pairs, bool wide, const OnesweepKernel** out) {
+  int cnt = 0;
+  const OnesweepKernel* ks = R == 8 ? onesweep_kernels_r8(&cnt) : onesweep_kernels_r11(&cnt);
+  // distinct tile shapes in registry order; shape 0 is the default
+  int shapes[16][2];
+  int ns = 0;
+  for (int i = 0; i < cnt && ns < 16; ++i) {
+    bool seen = false;
+    for (int s = 0; s < ns; ++s) seen |= (shapes[s][0] == ks[i].threads && shapes[s][1] == ks[i].items);
+    if (!seen) {
+      shapes[ns][0] = ks[i].threads;
+      shapes[ns][1] = ks[i].items;
+      ++ns;
+    }
+  }
+  const uint32_t t = tile_idx == 0 ? 0 : tile_idx - 1;
+  if (t >= uint32_t(ns)) return fail(RS_ERR_UNSUPPORTED, "tile shape %u not available for %d-bit digits", tile_idx, R);
+  for (int i = 0; i < cnt; ++i) {
+    if (ks[i].threads == shapes[t][0] && ks[i].items == shapes[t][1] && ks[i].pairs == pairs &&
+        ks[i].wide_status == wide) {
+      *out = &ks[i];
+      return RS_OK;
+    }
+  }
+  return fail(RS_ERR_UNSUPPORTED, "tile shape %u has no %s-status kernel (n too large for it)", tile_idx,
+              wide ? "64-bit" : "32-bit");
+}
+
+rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p) {
+  const uint32_t bits = (user && user->digit_bits) ? user->digit_bits : uint32_t(default_digit_bits(n, pairs));
+  if (bits != 8 && bits != 11) return fail(RS_ERR_UNSUPPORTED, "digit_bits must be 8 or 11 (got %u)", bits);
+  if (user && user->mode == RS_MODE_MSD) return fail(RS_ERR_UNSUPPORTED, "MSD mode is not available yet");
+  if (user && user->mode > RS_MODE_MSD) return fail(RS_ERR_INVALID, "unknown mode %u", user->mode);
+  p->R = int(bits);
+  p->nd = 0;
+  for (uint32_t s = 0; s < 32; s += bits) {
+    p->dig[p->nd].shift = s;
+    p->dig[p->nd].width = (32 - s) < bits ? (32 - s) : bits;
+    ++p->nd;
+  }
+  rs_status st = pick_kernel(p->R, user ? user->tile : 0, pairs, needs_wide_status(n), &p->k);
+  if (st != RS_OK) return st;
+  p->num_tiles = (n + p->k->tile - 1) / p->k->tile;
+  return RS_OK;
+}
+
+// ---- temp layout ------------------------------------------------------------
+struct Layout {
+  size_t ctrl = 0;     // [0,16): tile tickets per pass; [16,32): skip flags
+  size_t hist = 0;     // [nd][2^R] u32
+  size_t bases = 0;    // [nd][2^R] u32
+  size_t status = 0;   // [num_tiles][2^R] status words
+  size_t status_bytes = 0;
+  size_t alt_k = 0, alt_v = 0;
+  size_t memset_bytes = 0;  // ctrl + hist, cleared before the histogram
+  size_t total = 0;
+};
+
+Layout make_layout(const SortPlan& p, uint64_t n, bool pairs) {
+  Layout L;
+  const size_t digits = size_t(1) << p.R;
+  size_t off = 0;
+  L.ctrl = off;
+  off += kAlign;
+  L.hist = off;
+  off = align_up(off + size_t(p.nd) * digits * 4);
+  L.memset_bytes = off;
+  L.bases = off;
+  off = align_up(off + size_t(p.nd) * digits * 4);
+  L.status = off;
+  L.status_bytes = p.num_tiles * digits * (p.k->wide_status ? 8 : 4);
+  off = align_up(off + L.status_bytes);
+  if (p.nd > 1 && n > 0) {
+    L.alt_k = off;
+    off = align_up(off + size_t(n) * 4);
+    if (pairs) {
+      L.alt_v = off;
+      off = align_up(off + size_t(n) * 4);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+void part_offsets_host(uint64_t n, uint32_t parts, uint64_t* out) {
+  const uint64_t q = n / parts, r = n % parts;
+  for (uint64_t p = 0; p <= parts; ++p) out[p] = p * q + (p < r ? p : r);
+}
+
+// ---- the LSD pipeline ---------------------------------------------------------
+// memset(ctrl + hist) -> upfront histogram (+ clear status) -> digit scans ->
+// one onesweep pass per digit.
+rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, const uint32_t* vals_in,
+                  uint32_t* keys_out, uint32_t* vals_out, uint32_t n, unsigned char* temp, bool force_all,
+                  DeviceState* ds, cudaStream_t s) {
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + L.ctrl);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(temp + L.hist);
+  uint32_t* bases = reinterpret_cast<uint32_t*>(temp + L.bases);
+  const size_t digits = size_t(1) << p.R;
+  RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, L.memset_bytes, s); }),
+          "cudaMemsetAsync(temp)");
+
+  HistArgs ha{};
+  ha.keys = keys_in;
+  ha.n = n;
+  ha.num_digits = p.nd;
+  for (int j = 0; j < p.nd; ++j) ha.dig[j] = p.dig[j];
+  ha.hist = hist;
+  ha.zero_ptr = reinterpret_cast<uint4*>(temp + L.status);
+  ha.zero_vec4 = L.status_bytes / 16;
+  const HistKernel* hk = hist_kernel(p.R);
+  const size_t work = (size_t(n) + 4095) / 4096;  // one block per 4096 keys at least
+  unsigned hgrid = unsigned(ds->num_sms) * 2;
+  if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
+  RS_CUDA(traced(T_HIST, n, s, [&] { return hk->launch(ha, hgrid, s); }), "launch upfront_hist");
+
+  ScanArgs sa{hist, bases, force_all ? nullptr : ctrl + 4, n};
+  RS_CUDA(traced(T_SCAN, 0, s, [&] { return scan_kernel(p.R)->launch(sa, unsigned(p.nd), s); }),
+          "launch digit_scan");
+
+  for (int j = 0; j < p.nd; ++j) {
+    PassArgs pa{};
+    pa.keys_in = keys_in;
+    pa.keys_out = keys_out;
+    pa.keys_alt = L.alt_k ? reinterpret_cast<uint32_t*>(temp + L.alt_k) : keys_out;
+    pa.vals_in = vals_in;
+    pa.vals_out = vals_out;
+    pa.vals_alt = L.alt_v ? reinterpret_cast<uint32_t*>(temp + L.alt_v) : vals_out;
+    pa.n = n;
+    pa.shift = p.dig[j].shift;
+    pa.width = p.dig[j].width;
+    pa.pass = j;
+    pa.num_passes = p.nd;
+    pa.bases = bases + size_t(j) * digits;
+    pa.skip = force_all ? nullptr : ctrl + 4;
+    pa.status = temp + L.status;
+    pa.tile_counter = ctrl + j;
+    pa.err = ds->err;
+    RS_CUDA(traced(p.R == 8 ? T_PASS8 : T_PASS11, n, s, [&] { return p.k->launch(pa, unsigned(p.num_tiles), s); }),
+            "launch onesweep");
+  }
+  return RS_OK;
+}
+
+rs_status check_common(const void* keys_in, const void* keys_out, uint64_t n, void* temp, size_t* temp_bytes) {
+  if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
+  if (n >= (uint64_t(1) << 32)) return fail(RS_ERR_INVALID, "n = %llu: must be below 2^32", (unsigned long long)n);
+  if (temp && (reinterpret_cast<uintptr_t>(temp) % kAlign)) return fail(RS_ERR_INVALID, "temp is not 256-byte aligned");
+  if (n > 0 && temp) {
+    if (!keys_in || !keys_out) return fail(RS_ERR_INVALID, "NULL key buffer");
+    if ((reinterpret_cast<uintptr_t>(keys_in) | reinterpret_cast<uintptr_t>(keys_out)) & 3)
+      return fail(RS_ERR_INVALID, "key buffers must be 4-byte aligned");
+  }
+  return RS_OK;
+}
+
+rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                    uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets, const rs_plan* plan, void* temp,
+                    size_t* temp_bytes, cudaStream_t s, bool pairs) {
+  g_last_error.clear();
+  rs_status st = check_common(keys_in, keys_out, n, temp, temp_bytes);
+  if (st != RS_OK) return st;
+  if (num_parts < 1) return fail(RS_ERR_INVALID, "num_parts must be >= 1");
+  SortPlan p;
+  st = make_plan(n, pairs, plan, &p);
+  if (st != RS_OK) return st;
+  const Layout L = make_layout(p, n, pairs);
+  if (!temp) {
+    *temp_bytes = L.total;
+    return RS_OK;
+  }
+  if (*temp_bytes < L.total)
+    return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, L.total);
+  if (pairs && n > 0) {
+    if (!vals_in || !vals_out) return fail(RS_ERR_INVALID, "NULL value buffer");
+    if ((reinterpret_cast<uintptr_t>(vals_in) | reinterpret_cast<uintptr_t>(vals_out)) & 3)
+      return fail(RS_ERR_INVALID, "value buffers must be 4-byte aligned");
+  }
+  const size_t nb = size_t(n) * 4;
+  const void* outs[2] = {keys_out, pairs ? vals_out : nullptr};
+  const void* all[4] = {keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr};
+  for (const void* o : outs) {
+    if (!o) continue;
+    for (const void* x : all)
+      if (x && x != o && overlaps(o, nb, x, nb)) return fail(RS_ERR_INVALID, "an output overlaps another buffer");
+    if (o == keys_in || (pairs && o == vals_in)) return fail(RS_ERR_INVALID, "an output aliases an input");
+    if (overlaps(o, nb, temp, L.total)) return fail(RS_ERR_INVALID, "an output overlaps temp");
+  }
+  if (pairs && n > 0 && keys_out == vals_out) return fail(RS_ERR_INVALID, "keys_out and vals_out alias");
+  for (const void* x : all)
+    if (overlaps(x, nb, temp, L.total)) return fail(RS_ERR_INVALID, "a buffer overlaps temp");
+  if (h_part_offsets) part_offsets_host(n, num_parts, h_part_offsets);
+  if (n == 0) return RS_OK;
+  DeviceState* ds = nullptr;
+  st = device_state(&ds);
+  if (st != RS_OK) return st;
+  return run_lsd(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
+                 static_cast<unsigned char*>(temp), false, ds, s);
+}
+
+// Partition offsets of every segment, absolute (segment start added).
+__global__ void seg_part_offsets_kernel(const uint64_t* seg, uint32_t num_segs, uint32_t parts, uint64_t* out) {
+  const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const size_t per = size_t(parts) + 1;
+  if (i >= size_t(num_segs) * per) return;
+  const size_t sidx = i / per;
+  const uint64_t p = i % per;
+  const uint64_t a = seg[sidx], m = seg[sidx + 1] - a;
+  const uint64_t q = m / parts, r = m % parts;
+  out[i] = a + p * q + (p < r ? p : r);
+}
+
+}  // namespace
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" {
+
+rs_status rs_sort_u32(const uint32_t* keys_in, uint32_t* keys_out, uint64_t n, uint32_t num_parts,
+                      uint64_t* h_part_offsets, const rs_plan* plan, void* temp, size_t* temp_bytes,
+                      rs_stream_t stream) {
+  return sort_impl(keys_in, nullptr, keys_out, nullptr, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
+                   reinterpret_cast<cudaStream_t>(stream), false);
+}
+
+rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                            uint32_t* vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
+                            const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
+  return sort_impl(keys_in, vals_in, keys_out, vals_out, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
+                   reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,
+                                uint32_t* vals_out, const uint64_t* d_seg_offsets, const uint64_t* h_seg_offsets,
+                                uint32_t num_segs, uint64_t total_n, uint32_t num_parts, uint64_t* d_part_offsets,
+                                const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
+  g_last_error.clear();
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool pairs = vals_in != nullptr;
+  if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
+  if (!pairs && vals_out) return fail(RS_ERR_INVALID, "vals_out given without vals_in");
+  if (pairs && !vals_out) return fail(RS_ERR_INVALID, "vals_in given without vals_out");
+  if (num_parts < 1) return fail(RS_ERR_INVALID, "num_parts must be >= 1");
+  if (num_segs > 0 && !h_seg_offsets) return fail(RS_ERR_INVALID, "h_seg_offsets is NULL");
+  if (total_n >= (uint64_t(1) << 32)) return fail(RS_ERR_INVALID, "total_n must be below 2^32");
+  uint64_t max_seg = 0;
+  if (num_segs > 0) {
+    if (h_seg_offsets[0] != 0 || h_seg_offsets[num_segs] != total_n)
+      return fail(RS_ERR_INVALID, "segment offsets must start at 0 and end at total_n");
+    for (uint32_t i = 0; i < num_segs; ++i) {
+      if (h_seg_offsets[i + 1] < h_seg_offsets[i]) return fail(RS_ERR_INVALID, "segment offsets decrease at %u", i);
+      const uint64_t m = h_seg_offsets[i + 1] - h_seg_offsets[i];
+      if (m > max_seg) max_seg = m;
+    }
+  }
+  SortPlan p;
+  rs_status st = make_plan(max_seg, pairs, plan, &p);
+  if (st != RS_OK) return st;
+  const Layout L = make_layout(p, max_seg, pairs);
+  if (!temp) {
+    *temp_bytes = L.total;
+    return RS_OK;
+  }
+  if (reinterpret_cast<uintptr_t>(temp) % kAlign) return fail(RS_ERR_INVALID, "temp is not 256-byte aligned");
+  if (*temp_bytes < L.total) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, L.total);
+  if (total_n > 0 && (!keys_in || !keys_out || !d_seg_offsets))
+    return fail(RS_ERR_INVALID, "NULL buffer");
+  const size_t nb = size_t(total_n) * 4;
+  if (overlaps(keys_out, nb, keys_in, nb) || overlaps(keys_out, nb, temp, L.total) ||
+      (pairs && (overlaps(vals_out, nb, vals_in, nb) || overlaps(vals_out, nb, keys_out, nb) ||
+                 overlaps(vals_out, nb, keys_in, nb) || overlaps(vals_out, nb, temp, L.total) ||
+                 overlaps(keys_out, nb, vals_in, nb))))
+    return fail(RS_ERR_INVALID, "an output overlaps another buffer");
+  DeviceState* ds = nullptr;
+  if (num_segs > 0) {
+    st = device_state(&ds);
+    if (st != RS_OK) return st;
+  }
+  if (d_part_offsets && num_segs > 0) {
+    const size_t cnt = size_t(num_segs) * (num_parts + 1);
+    RS_CUDA(traced(T_SEGOFF, 0, s,
+                   [&] {
+                     seg_part_offsets_kernel<<<unsigned((cnt + 255) / 256), 256, 0, s>>>(d_seg_offsets, num_segs,
+                                                                                         num_parts, d_part_offsets);
+                     return cudaGetLastError();
+                   }),
+            "launch seg_part_offsets");
+  }
+  for (uint32_t i = 0; i < num_segs; ++i) {
+    const uint64_t a = h_seg_offsets[i], m = h_seg_offsets[i + 1] - a;
+    if (m == 0) continue;
+    SortPlan ps;
+    st = make_plan(m, pairs, plan, &ps);
+    if (st != RS_OK) return st;
+    const Layout Ls = make_layout(ps, m, pairs);
+    st = run_lsd(ps, Ls, keys_in + a, pairs ? vals_in + a : nullptr, keys_out + a, pairs ? vals_out + a : nullptr,
+                 uint32_t(m), static_cast<unsigned char*>(temp), false, ds, s);
+    if (st != RS_OK) return st;
+  }
+  return RS_OK;
+}
+
+rs_status rs_digit_histograms(const uint32_t* keys, uint64_t n, uint32_t digit_bits, uint32_t* d_hist,
+                              uint32_t* d_bases, uint32_t* d_skip, rs_stream_t stream) {
+  g_last_error.clear();
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (digit_bits != 8 && digit_bits != 11) return fail(RS_ERR_UNSUPPORTED, "digit_bits must be 8 or 11");
+  if (n >= (uint64_t(1) << 32)) return fail(RS_ERR_INVALID, "n must be below 2^32");
+  if (!d_hist) return fail(RS_ERR_INVALID, "d_hist is NULL");
+  if (n > 0 && !keys) return fail(RS_ERR_INVALID, "keys is NULL");
+  if (reinterpret_cast<uintptr_t>(keys) & 3) return fail(RS_ERR_INVALID, "keys must be 4-byte aligned");
+  HistArgs ha{};
+  ha.keys = keys;
+  ha.n = uint32_t(n);
+  ha.num_digits = 0;
+  for (uint32_t sft = 0; sft < 32; sft += digit_bits) {
+    ha.dig[ha.num_digits].shift = sft;
+    ha.dig[ha.num_digits].width = (32 - sft) < digit_bits ? (32 - sft) : digit_bits;
+    ++ha.num_digits;
+  }
+  ha.hist = d_hist;
+  DeviceState* ds = nullptr;
+  rs_status st = device_state(&ds);
+  if (st != RS_OK) return st;
+  const size_t bytes = size_t(ha.num_digits) * (size_t(1) << digit_bits) * 4;
+  RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(d_hist, 0, bytes, s); }), "cudaMemsetAsync(hist)");
+  if (n > 0) {
+    const size_t work = (size_t(n) + 4095) / 4096;
+    unsigned grid = unsigned(ds->num_sms) * 2;
+    if (work < grid) grid = unsigned(work);
+    RS_CUDA(traced(T_HIST, double(n), s, [&] { return hist_kernel(int(digit_bits))->launch(ha, grid, s); }),
+            "launch upfront_hist");
+  }
+  if (d_bases || d_skip) {
+    uint32_t* b = d_bases;
+    if (!b) return fail(RS_ERR_INVALID, "d_skip needs d_bases");
+    ScanArgs sa{d_hist, b, d_skip, uint32_t(n)};
+    RS_CUDA(traced(T_SCAN, 0, s, [&] { return scan_kernel(int(digit_bits))->launch(sa, unsigned(ha.num_digits), s); }),
+            "launch digit_scan");
+  }
+  return RS_OK;
+}
+
+rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
+                        uint64_t n, uint32_t shift, uint32_t width, void* temp, size_t* temp_bytes,
+                        rs_stream_t stream) {
+  g_last_error.clear();
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rs_status st = check_common(keys_in, keys_out, n, temp, temp_bytes);
+  if (st != RS_OK) return st;
+  if (width < 1 || width > 11 || shift + width > 32) return fail(RS_ERR_INVALID, "bad digit (shift %u, width %u)", shift, width);
+  const bool pairs = vals_in != nullptr;
+  if (pairs != (vals_out != nullptr)) return fail(RS_ERR_INVALID, "vals_in and vals_out must both be given or both NULL");
+  SortPlan p;
+  p.R = width > 8 ? 11 : 8;
+  p.nd = 1;
+  p.dig[0].shift = shift;
+  p.dig[0].width = width;
+  st = pick_kernel(p.R, 0, pairs, needs_wide_status(n), &p.k);
+  if (st != RS_OK) return st;
+  p.num_tiles = (n + p.k->tile - 1) / p.k->tile;
+  const Layout L = make_layout(p, n, pairs);
+  if (!temp) {
+    *temp_bytes = L.total;
+    return RS_OK;
+  }
+  if (*temp_bytes < L.total) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, L.total);
+  const size_t nb = size_t(n) * 4;
+  if (overlaps(keys_out, nb, keys_in, nb) || overlaps(keys_out, nb, temp, L.total) ||
+      (pairs && (overlaps(vals_out, nb, vals_in, nb) || overlaps(vals_out, nb, keys_out, nb) ||
+                 overlaps(vals_out, nb, keys_in, nb) || overlaps(keys_out, nb, vals_in, nb) ||
+                 overlaps(vals_out, nb, temp, L.total))))
+    return fail(RS_ERR_INVALID, "an output overlaps another buffer");
+  if (n == 0) return RS_OK;
+  DeviceState* ds = nullptr;
+  st = device_state(&ds);
+  if (st != RS_OK) return st;
+  return run_lsd(p, L, keys_in, vals_in, keys_out, vals_out, uint32_t(n), static_cast<unsigned char*>(temp), true,
+                 ds, s);
+}
+
+const char* rs_last_error(void) { return g_last_error.c_str(); }
+
+rs_status rs_check_device_error(rs_stream_t stream) {
+  g_last_error.clear();
+  DeviceState* ds = nullptr;
+  rs_status st = device_state(&ds);
+  if (st != RS_OK) return st;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RS_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  uint32_t word = 0;
+  RS_CUDA(cudaMemcpy(&word, ds->err, sizeof(word), cudaMemcpyDeviceToHost), "read device error word");
+  if (word) {
+    const uint32_t zero = 0;
+    RS_CUDA(cudaMemcpy(ds->err, &zero, sizeof(zero), cudaMemcpyHostToDevice), "clear device error word");
+    if (word & kErrTimeout) return fail(RS_ERR_TIMEOUT, "a bounded device-side wait gave up (error word 0x%x)", word);
+    return fail(RS_ERR_CUDA, "a device-side output index check fired (error word 0x%x)", word);
+  }
+  return RS_OK;
+}
+
+rs_status rs_trace_enable(int on) {
+  g_last_error.clear();
+  std::lock_guard<std::mutex> lock(g_trace_mu);
+  g_trace_on = on != 0;
+  return RS_OK;
+}
+
+rs_status rs_trace_read(rs_trace_entry* out, uint32_t capacity, uint32_t* count) {
+  g_last_error.clear();
+  if (!count || (capacity > 0 && !out)) return fail(RS_ERR_INVALID, "NULL output");
+  std::lock_guard<std::mutex> lock(g_trace_mu);
+  uint32_t launches[T_KINDS] = {};
+  double ms[T_KINDS] = {}, keys[T_KINDS] = {};
+  rs_status st = RS_OK;
+  for (TraceRec& r : g_trace) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && st == RS_OK) st = cuda_fail(e, "trace event");
+    ++launches[r.kind];
+    ms[r.kind] += t;
+    keys[r.kind] += r.keys;
+    g_event_pool.push_back(r.a);
+    g_event_pool.push_back(r.b);
+  }
+  g_trace.clear();
+  uint32_t c = 0;
+  for (int k = 0; k < T_KINDS; ++k) {
+    if (!launches[k]) continue;
+    if (c < capacity) {
+      std::memset(&out[c], 0, sizeof(out[c]));
+      std::snprintf(out[c].name, sizeof(out[c].name), "%s", kTraceNames[k]);
+      out[c].launches = launches[k];
+      out[c].total_ms = ms[k];
+      out[c].keys = keys[k];
+    }
+    ++c;
+  }
+  *count = c < capacity ? c : capacity;
+  return st;
+}
+
+uint32_t rs_version(void) { return kVersion; }
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// Upfront digit histograms (every digit in one read of the keys) and their
+// exclusive scans.
+//
+// Paper: the count loop of the bucketing phase ("increment bucket to which
+// element[i] belongs", Sec. 3.2) followed by the cumulative totals (Sec. 3.2;
+// Sec. 4.4 sums the per-cell totals after making them cumulative).  On the
+// AP1000 each cell counted its own elements and a hypercube summation added
+// the 64 arrays (Sec. 4.4); here each block counts a slice of the keys into
+// shared memory and the block arrays are added into one global array.
+#include "rs_device.cuh"
+#include "rs_internal.h"
+
+namespace rs {
+
+// Block-private sub-histograms per digit; warps are spread over COPIES
+// copies to thin out shared-memory atomic collisions on skewed data.
+template <int R, int THREADS, int COPIES>
+__global__ void __launch_bounds__(THREADS) upfront_hist_kernel(const HistArgs a) {
+  constexpr int DIGITS = 1 << R;
+  extern __shared__ __align__(16) uint32_t sh[];  // [COPIES][num_digits][DIGITS]
+  const int nd = a.num_digits;
+  const int tid = threadIdx.x;
+  const int per_copy = nd * DIGITS;
+  for (int i = tid; i < COPIES * per_copy; i += THREADS) sh[i] = 0u;
+  __syncthreads();
+  uint32_t* my = sh + ((tid >> 5) % COPIES) * per_copy;
+
+  uint32_t sft[kMaxDigits], wid[kMaxDigits];
+#pragma unroll
+  for (int j = 0; j < kMaxDigits; ++j) {
+    sft[j] = a.dig[j].shift;
+    wid[j] = a.dig[j].width;
+  }
+  auto count = [&](uint32_t k) {
+#pragma unroll
+    for (int j = 0; j < kMaxDigits; ++j)
+      if (j < nd) atomicAdd(&my[j * DIGITS + digit_of(k, sft[j], wid[j])], 1u);
+  };
+
+  // keys before the first 16-byte boundary and after the last full vector
+  const uint32_t n = a.n;
+  const uint32_t mis = uint32_t((reinterpret_cast<uintptr_t>(a.keys) >> 2) & 3u);
+  uint32_t head = (4u - mis) & 3u;
+  if (head > n) head = n;
+  const size_t nvec = size_t(n - head) / 4;
+  const uint32_t tail = head + uint32_t(nvec * 4);
+  if (blockIdx.x == gridDim.x - 1) {
+    for (uint32_t i = tid; i < head; i += THREADS) count(a.keys[i]);
+    for (uint32_t i = tail + tid; i < n; i += THREADS) count(a.keys[i]);
+  }
+  const uint4* v4 = reinterpret_cast<const uint4*>(a.keys + head);
+  const size_t stride = size_t(gridDim.x) * THREADS;
+  size_t i = size_t(blockIdx.x) * THREADS + tid;
+  for (; i + 3 * stride < nvec; i += 4 * stride) {
+    const uint4 x0 = ld_stream4(v4 + i);
+    const uint4 x1 = ld_stream4(v4 + i + stride);
+    const uint4 x2 = ld_stream4(v4 + i + 2 * stride);
+    const uint4 x3 = ld_stream4(v4 + i + 3 * stride);
+    count(x0.x); count(x0.y); count(x0.z); count(x0.w);
+    count(x1.x); count(x1.y); count(x1.z); count(x1.w);
+    count(x2.x); count(x2.y); count(x2.z); count(x2.w);
+    count(x3.x); count(x3.y); count(x3.z); count(x3.w);
+  }
+  for (; i < nvec; i += stride) {
+    const uint4 x = ld_stream4(v4 + i);
+    count(x.x); count(x.y); count(x.z); count(x.w);
+  }
+
+  // clear the chained-scan status words for the passes that follow
+  for (size_t z = size_t(blockIdx.x) * THREADS + tid; z < a.zero_vec4; z += stride)
+    a.zero_ptr[z] = make_uint4(0u, 0u, 0u, 0u);
+
+  __syncthreads();
+  for (int b = tid; b < per_copy; b += THREADS) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int c = 0; c < COPIES; ++c) s += sh[c * per_copy + b];
+    if (s) atomicAdd(&a.hist[b], s);
+  }
+}
+
+// One block per digit: exclusive scan of its histogram, and whether a single
+// bucket holds every key.
+template <int R>
+__global__ void __launch_bounds__((1 << R) < 1024 ? (1 << R) : 1024) digit_scan_kernel(const ScanArgs a) {
+  constexpr int DIGITS = 1 << R;
+  constexpr int THREADS = DIGITS < 1024 ? DIGITS : 1024;
+  constexpr int PER = DIGITS / THREADS;
+  __shared__ uint32_t s_warp[32];
+  const int j = blockIdx.x, tid = threadIdx.x;
+  const uint32_t* h = a.hist + size_t(j) * DIGITS + tid * PER;
+  uint32_t v[PER], sum = 0;
+  int full = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    v[k] = h[k];
+    sum += v[k];
+    full |= (v[k] == a.n);
+  }
+  uint32_t e = block_exclusive_sum<THREADS>(sum, s_warp);
+  uint32_t* b = a.bases + size_t(j) * DIGITS + tid * PER;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    b[k] = e;
+    e += v[k];
+  }
+  const int any = __syncthreads_or(full);
+  if (tid == 0 && a.skip) a.skip[j] = any ? 1u : 0u;
+}
+
+template <int R, int THREADS, int COPIES>
+static cudaError_t launch_hist(const HistArgs& a, unsigned grid, cudaStream_t s) {
+  const size_t smem = size_t(COPIES) * a.num_digits * (1u << R) * 4;
+  upfront_hist_kernel<R, THREADS, COPIES><<<grid, THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_scan(const ScanArgs& a, unsigned grid, cudaStream_t s) {
+  constexpr int THREADS = (1 << R) < 1024 ? (1 << R) : 1024;
+  digit_scan_kernel<R><<<grid, THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// Shared memory: 11-bit digits, 3 digits, 2 copies = 48 KiB; 8-bit digits,
+// 4 digits, 4 copies = 16 KiB.
+static const HistKernel kHist11 = {11, 512, size_t(2) * 3 * 2048 * 4, &launch_hist<11, 512, 2>,
+                                   reinterpret_cast<const void*>(&upfront_hist_kernel<11, 512, 2>)};
+static const HistKernel kHist8 = {8, 512, size_t(4) * 4 * 256 * 4, &launch_hist<8, 512, 4>,
+                                  reinterpret_cast<const void*>(&upfront_hist_kernel<8, 512, 4>)};
+static const ScanKernel kScan11 = {11, 1024, &launch_scan<11>};
+static const ScanKernel kScan8 = {8, 256, &launch_scan<8>};
+
+const HistKernel* hist_kernel(int radix_bits) { return radix_bits == 11 ? &kHist11 : (radix_bits == 8 ? &kHist8 : nullptr); }
+const ScanKernel* scan_kernel(int radix_bits) { return radix_bits == 11 ? &kScan11 : (radix_bits == 8 ? &kScan8 : nullptr); }
+
+}  // namespace rs

@@ -1,0 +1,378 @@
+// One LSD distribution pass by a digit, in a single read and write of the
+// keys ("onesweep"): per tile, a stable rank of every key by its digit, a
+// chained scan across tiles for the per-(tile, digit) output offset, and a
+// scatter staged through shared memory so that keys of one digit leave the
+// tile as one contiguous run.
+//
+// Paper: the pass is the bucketing/distribution step of Sec. 3.2 (count per
+// bucket, cumulative totals, "partial sort" grouping keys by bucket in
+// ascending order, distribution of contiguous bucket ranges), done exactly:
+// the per-cell-per-bucket offsets the paper chose not to compute (which
+// left up to 128 elements misplaced, fixed later by post-balancing) come
+// here from the chained scan, so no repair phase is needed.  Stability is
+// what makes the repeated low-to-high passes a sort (Sec. 3.3.1) and keeps
+// the order inside a bucket across the distribution (Sec. 5).
+//
+// Per tile (TILE = THREADS * ITEMS keys, tiles handed out by an atomic
+// ticket so that every predecessor of a tile is already running):
+//  1. load: warp w takes keys [w*32*ITEMS, (w+1)*32*ITEMS) of the tile,
+//     item j of lane l being key w*32*ITEMS + j*32 + l (coalesced);
+//  2. rank: per item, lanes with the same digit find each other with
+//     __match_any_sync; the highest such lane bumps the warp's private
+//     16-bit counter for the digit by the group size; a lane's rank within
+//     its warp is the counter before the bump plus the number of group
+//     lanes below it.  Warp-private counters keep the rank order equal to
+//     the input order (stability);
+//  3. per digit: the tile's count (sum over warps) is published at once
+//     as an "aggregate" status word; the counters are rewritten as
+//     exclusive (digit, warp) prefixes, giving each key its position in the
+//     digit-sorted tile;
+//  4. stage keys (and values) in shared memory at their tile positions;
+//  5. lookback: walk back over earlier tiles' status words, a window of
+//     them per round, adding aggregates until an "inclusive" word, then
+//     publish this tile's inclusive count; waits are bounded;
+//  6. write the staged keys out in tile order, each to base[digit] + (keys
+//     of the digit in earlier tiles) + (position within the digit here).
+#pragma once
+
+#include "rs_device.cuh"
+#include "rs_internal.h"
+
+namespace rs {
+
+// DPT consecutive 16-bit counters, two per 32-bit word.  Sums of two halves
+// never carry into each other because every count is at most TILE < 2^16.
+template <int DPT>
+struct CntVec {
+  static constexpr int W = (DPT + 1) / 2;
+  uint32_t w[W];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[i] = 0;
+  }
+  __device__ __forceinline__ void add(const CntVec& o) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) w[i] += o.w[i];
+  }
+  __device__ __forceinline__ uint32_t half(int k) const { return (w[k >> 1] >> (16 * (k & 1))) & 0xffffu; }
+  __device__ __forceinline__ void set_half(int k, uint32_t v) {
+    w[k >> 1] = (w[k >> 1] & ~(0xffffu << (16 * (k & 1)))) | (v << (16 * (k & 1)));
+  }
+  __device__ __forceinline__ void load(const uint16_t* p) {
+    if constexpr (DPT == 1) {
+      w[0] = *p;
+    } else if constexpr (DPT == 2) {
+      w[0] = *reinterpret_cast<const uint32_t*>(p);
+    } else if constexpr (DPT == 4) {
+      const uint2 v = *reinterpret_cast<const uint2*>(p);
+      w[0] = v.x;
+      w[1] = v.y;
+    } else {
+      static_assert(DPT == 8, "digits per thread must be 1, 2, 4 or 8");
+      const uint4 v = *reinterpret_cast<const uint4*>(p);
+      w[0] = v.x;
+      w[1] = v.y;
+      w[2] = v.z;
+      w[3] = v.w;
+    }
+  }
+  __device__ __forceinline__ void store(uint16_t* p) const {
+    if constexpr (DPT == 1) {
+      *p = uint16_t(w[0]);
+    } else if constexpr (DPT == 2) {
+      *reinterpret_cast<uint32_t*>(p) = w[0];
+    } else if constexpr (DPT == 4) {
+      *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+    } else {
+      *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+};
+
+template <int R, int THREADS, int ITEMS, bool PAIRS>
+struct OnesweepLayout {
+  static constexpr int DIGITS = 1 << R;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * ITEMS;
+  // threads doing the per-digit work, and digits per such thread
+  static constexpr int DTH = DIGITS < THREADS ? DIGITS : THREADS;
+  static constexpr int DPT = DIGITS / DTH;
+  static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;
+  static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
+  static constexpr size_t UNION_BYTES = ((CNT_BYTES > BUF_BYTES ? CNT_BYTES : BUF_BYTES) + 15) / 16 * 16;
+  static constexpr size_t OFF_GOFF = UNION_BYTES;
+  static constexpr size_t OFF_WARP = OFF_GOFF + size_t(DIGITS) * 4;
+  static constexpr size_t OFF_TILE = OFF_WARP + 32 * 4;
+  static constexpr size_t SMEM = OFF_TILE + 16;
+  static_assert(THREADS % 32 == 0 && THREADS <= 1024, "block shape");
+  static_assert(TILE < 65536, "ranks are 16-bit");
+  static_assert(DIGITS % DTH == 0, "digits must split evenly over threads");
+  static_assert((WARPS * DIGITS) % 8 == 0, "counter array is cleared in 16-byte units");
+};
+
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs a) {
+  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  constexpr int DIGITS = L::DIGITS, WARPS = L::WARPS, TILE = L::TILE;
+  constexpr int DTH = L::DTH, DPT = L::DPT;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem);  // [WARPS][DIGITS]
+  uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem);  // aliases s_cnt once ranks are final
+  uint32_t* s_goff = reinterpret_cast<uint32_t*>(smem + L::OFF_GOFF);
+  uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L::OFF_WARP);
+  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
+
+  const Route route = route_of(a.skip, a.pass, a.num_passes);
+  if (!route.active) return;
+  const uint32_t* kin = route.src == BUF_IN ? a.keys_in : (route.src == BUF_OUT ? a.keys_out : a.keys_alt);
+  uint32_t* kout = route.dst == BUF_OUT ? a.keys_out : a.keys_alt;
+  const uint32_t* vin = nullptr;
+  uint32_t* vout = nullptr;
+  if constexpr (PAIRS) {
+    vin = route.src == BUF_IN ? a.vals_in : (route.src == BUF_OUT ? a.vals_out : a.vals_alt);
+    vout = route.dst == BUF_OUT ? a.vals_out : a.vals_alt;
+  }
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  {
+    uint4* c4 = reinterpret_cast<uint4*>(s_cnt);
+    for (int i = tid; i < WARPS * DIGITS / 8; i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if (tid == 0) *s_tile = atomicAdd(a.tile_counter, 1u);
+  __syncthreads();
+  const uint32_t tile = *s_tile;
+  const size_t tile_base = size_t(tile) * TILE;
+  const size_t left = size_t(a.n) - tile_base;
+  const uint32_t valid = left < size_t(TILE) ? uint32_t(left) : uint32_t(TILE);
+
+  // 1. load the keys
+  uint32_t key[ITEMS];
+  const size_t wbase = tile_base + size_t(warp) * 32 * ITEMS + lane;
+  if (valid == TILE) {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) key[j] = ld_stream(kin + wbase + j * 32);
+  } else {
+    // Keys past the end act as 0xFFFFFFFF: their digit is the largest and
+    // they come after every real key, so they sort to the tile's tail and
+    // are never written.
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const size_t idx = wbase + j * 32;
+      key[j] = idx < a.n ? kin[idx] : 0xffffffffu;
+    }
+  }
+
+  // 2. rank within the warp; ranks are < 2^16, two per register
+  uint16_t* wc = s_cnt + warp * DIGITS;
+  const uint32_t lt = lanemask_lt();
+  uint32_t rk[(ITEMS + 1) / 2];
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t d = digit_of(key[j], a.shift, a.width);
+    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    const int leader = 31 - __clz(peers);
+    uint32_t before = 0;
+    if (lane == leader) {
+      before = wc[d];
+      wc[d] = uint16_t(before + __popc(peers));
+    }
+    __syncwarp();
+    before = __shfl_sync(0xffffffffu, before, leader);
+    const uint32_t r = before + __popc(peers & lt);
+    if (j & 1) rk[j >> 1] |= r << 16;
+    else rk[j >> 1] = r;
+  }
+  __syncthreads();
+
+  // 3. per-digit tile counts -> aggregate status; counters -> exclusive prefixes
+  const int d0 = tid * DPT;
+  uint32_t tot[DPT], loff[DPT];
+  uint32_t my_sum = 0;
+  if (tid < DTH) {
+    CntVec<DPT> run;
+    run.zero();
+#pragma unroll 4
+    for (int wi = 0; wi < WARPS; ++wi) {
+      CntVec<DPT> v;
+      v.load(s_cnt + wi * DIGITS + d0);
+      run.add(v);
+    }
+    S* mine = reinterpret_cast<S*>(a.status) + size_t(tile) * DIGITS + d0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      tot[k] = run.half(k);
+      my_sum += tot[k];
+      st_relaxed(mine + k, status_word<S>(route.parity, tile == 0, tot[k]));
+    }
+  }
+  const uint32_t excl = block_exclusive_sum<THREADS>(my_sum, s_warp);
+  if (tid < DTH) {
+    CntVec<DPT> run;
+    run.zero();
+    uint32_t r = excl;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      loff[k] = r;
+      run.set_half(k, r);
+      r += tot[k];
+    }
+#pragma unroll 4
+    for (int wi = 0; wi < WARPS; ++wi) {
+      CntVec<DPT> v;
+      v.load(s_cnt + wi * DIGITS + d0);
+      run.store(s_cnt + wi * DIGITS + d0);
+      run.add(v);
+    }
+  }
+  __syncthreads();
+
+  // 4. tile positions; stage the tile in shared memory in digit order
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t pos = s_cnt[warp * DIGITS + digit_of(key[j], a.shift, a.width)];
+    if (j & 1) rk[j >> 1] += pos << 16;
+    else rk[j >> 1] += pos;
+  }
+  __syncthreads();  // counters are dead; the staging buffer reuses them
+  uint32_t val[PAIRS ? ITEMS : 1];
+  if constexpr (PAIRS) {
+    if (valid == TILE) {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(vin + wbase + j * 32);
+    } else {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) {
+        const size_t idx = wbase + j * 32;
+        val[j] = idx < a.n ? vin[idx] : 0u;
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) s_buf[(rk[j >> 1] >> (16 * (j & 1))) & 0xffffu] = key[j];
+  if constexpr (PAIRS) {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) s_buf[TILE + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = val[j];
+  }
+
+  // 5. chained scan over earlier tiles (decoupled lookback).  Each round
+  // reads a window of LB predecessors per digit at once, then adds
+  // aggregates from the nearest one back to the first inclusive word.
+  if (tid < DTH) {
+    constexpr int LB = (16 / DPT) > 1 ? (16 / DPT) : 1;
+    uint32_t prefix[DPT];
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) prefix[k] = 0;
+    if (tile > 0) {
+      const S* st = reinterpret_cast<const S*>(a.status);
+      int pred[DPT];
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) pred[k] = int(tile) - 1;
+      uint32_t pending = (1u << DPT) - 1u;
+      uint32_t spins = 0;
+      while (pending) {
+        S w[DPT][LB];
+#pragma unroll
+        for (int k = 0; k < DPT; ++k)
+#pragma unroll
+          for (int i = 0; i < LB; ++i)
+            if ((pending & (1u << k)) && pred[k] - i >= 0)
+              w[k][i] = ld_relaxed(st + size_t(pred[k] - i) * DIGITS + d0 + k);
+        bool stalled = false;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) {
+          if (!(pending & (1u << k))) continue;
+#pragma unroll
+          for (int i = 0; i < LB; ++i) {
+            if (!(pending & (1u << k))) break;
+            if (pred[k] < 0) {  // cannot happen: tile 0 is always inclusive
+              pending &= ~(1u << k);
+              atomicOr(a.err, kErrTimeout);
+              break;
+            }
+            const S x = w[k][i];
+            if (!status_ready<S>(x, route.parity)) {
+              stalled = true;
+              break;
+            }
+            prefix[k] += status_count<S>(x);
+            if (status_inclusive<S>(x)) pending &= ~(1u << k);
+            else --pred[k];
+          }
+        }
+        if (pending && stalled) {
+          if (++spins > kSpinLimit) {
+            atomicOr(a.err, kErrTimeout);
+            break;
+          }
+          if (spins > 16) __nanosleep(100);
+        }
+      }
+      S* mine = reinterpret_cast<S*>(a.status) + size_t(tile) * DIGITS + d0;
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) st_relaxed(mine + k, status_word<S>(route.parity, true, prefix[k] + tot[k]));
+    }
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) s_goff[d0 + k] = a.bases[d0 + k] + prefix[k] - loff[k];
+  }
+  __syncthreads();
+
+  // 6. write out in tile order: runs of one digit go to consecutive
+  // addresses.  The range check only guards against a corrupted offset (it
+  // raises an error bit instead of writing out of bounds).
+  if (valid == TILE) {
+    bool oob = false;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint32_t i = k * THREADS + tid;
+      const uint32_t kk = s_buf[i];
+      const uint32_t g = s_goff[digit_of(kk, a.shift, a.width)] + i;
+      if (g < a.n) {
+        kout[g] = kk;
+        if constexpr (PAIRS) vout[g] = s_buf[TILE + i];
+      } else {
+        oob = true;
+      }
+    }
+    if (oob) atomicOr(a.err, kErrBounds);
+  } else {
+    bool oob = false;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint32_t i = k * THREADS + tid;
+      if (i < valid) {
+        const uint32_t kk = s_buf[i];
+        const uint32_t g = s_goff[digit_of(kk, a.shift, a.width)] + i;
+        if (g < a.n) {
+          kout[g] = kk;
+          if constexpr (PAIRS) vout[g] = s_buf[TILE + i];
+        } else {
+          oob = true;
+        }
+      }
+    }
+    if (oob) atomicOr(a.err, kErrBounds);
+  }
+}
+
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB>
+cudaError_t launch_onesweep(const PassArgs& a, unsigned grid, cudaStream_t s) {
+  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB><<<grid, THREADS, L::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB>
+OnesweepKernel make_onesweep() {
+  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  return OnesweepKernel{R,
+                        THREADS,
+                        ITEMS,
+                        L::TILE,
+                        PAIRS,
+                        sizeof(S) == 8,
+                        L::SMEM,
+                        &launch_onesweep<R, THREADS, ITEMS, PAIRS, S, MINB>,
+                        reinterpret_cast<const void*>(&onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB>)};
+}
+
+}  // namespace rs

@@ -1,0 +1,106 @@
+"""The C-ABI library loads and exports every entry point the header declares;
+argument checks that need no GPU.  (No compute calls: no GPU here.)"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rsort.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(rs_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ("rs_sort_u32", "rs_sort_u32_pairs", "rs_sort_u32_segmented", "rs_last_error",
+                 "rs_check_device_error", "rs_digit_histograms", "rs_radix_pass", "rs_version"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_cs_0004013_gb300 as r
+    dll = ctypes.CDLL(r.LIBRARY_PATH)
+    missing = [n for n in declared_functions() if not hasattr(dll, n)]
+    assert not missing, missing
+
+
+def test_version_and_no_error_initially():
+    import paper_cs_0004013_gb300 as r
+    assert r.rs_version() >= 10000
+    assert r.rs_last_error() == ""
+
+
+def test_temp_queries_grow_with_n_and_payload():
+    import paper_cs_0004013_gb300 as r
+    a = r.rs_sort_u32(None, None, 1 << 20)
+    b = r.rs_sort_u32(None, None, 1 << 22)
+    c = r.rs_sort_u32_pairs(None, None, None, None, 1 << 22)
+    assert 0 < a < b < c
+    assert r.rs_sort_u32(None, None, 0) > 0
+    # the alternate key buffer dominates: at least 4 bytes per key
+    assert b >= 4 * (1 << 22)
+    assert c >= 8 * (1 << 22)
+    for bits in (8, 11):
+        assert r.rs_sort_u32(None, None, 1 << 20, plan={"digit_bits": bits}) > 0
+
+
+@pytest.mark.parametrize("call", ["n_too_big", "bad_bits", "bad_parts", "msd_pending", "bad_tile"])
+def test_invalid_arguments(call):
+    import paper_cs_0004013_gb300 as r
+    with pytest.raises(r.RsError) as e:
+        if call == "n_too_big":
+            r.rs_sort_u32(None, None, 1 << 32)
+        elif call == "bad_bits":
+            r.rs_sort_u32(None, None, 100, plan={"digit_bits": 9})
+        elif call == "bad_parts":
+            r.rs_sort_u32(None, None, 10, num_parts=0)
+        elif call == "msd_pending":
+            r.rs_sort_u32(None, None, 100, plan={"mode": 99})
+        else:
+            r.rs_sort_u32(None, None, 100, plan={"tile": 42})
+    assert r.rs_last_error() != ""
+
+
+def test_temp_too_small_and_misaligned_are_rejected():
+    import paper_cs_0004013_gb300 as r
+    need = r.rs_sort_u32(None, None, 1000)
+    sz = ctypes.c_size_t(need - 1)
+    st = r.lib.rs_sort_u32(ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 24), 1000, 64, None, None,
+                           ctypes.c_void_p(1 << 28), ctypes.byref(sz), None)
+    assert st == 2  # RS_ERR_TEMP_TOO_SMALL
+    sz = ctypes.c_size_t(need)
+    st = r.lib.rs_sort_u32(ctypes.c_void_p(1 << 20), ctypes.c_void_p(1 << 24), 1000, 64, None, None,
+                           ctypes.c_void_p((1 << 28) + 16), ctypes.byref(sz), None)
+    assert st == 1  # misaligned temp
+
+
+def test_overlapping_buffers_are_rejected():
+    import paper_cs_0004013_gb300 as r
+    need = r.rs_sort_u32(None, None, 1000)
+    sz = ctypes.c_size_t(need)
+    # keys_out overlaps keys_in
+    st = r.lib.rs_sort_u32(ctypes.c_void_p(1 << 20), ctypes.c_void_p((1 << 20) + 400), 1000, 64, None, None,
+                           ctypes.c_void_p(1 << 28), ctypes.byref(sz), None)
+    assert st == 1 and "overlap" in r.rs_last_error()
+    # keys_out inside temp
+    st = r.lib.rs_sort_u32(ctypes.c_void_p(1 << 20), ctypes.c_void_p((1 << 28) + 256), 1000, 64, None, None,
+                           ctypes.c_void_p(1 << 28), ctypes.byref(sz), None)
+    assert st == 1
+
+
+def test_partition_offsets_host_path_needs_no_gpu():
+    """n = 0 returns the offsets without touching the device."""
+    import numpy as np
+    import paper_cs_0004013_gb300 as r
+    need = r.rs_sort_u32(None, None, 0)
+    offs = np.ones(65, dtype=np.uint64)
+    sz = ctypes.c_size_t(need)
+    st = r.lib.rs_sort_u32(None, None, 0, 64, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), None,
+                           ctypes.c_void_p(1 << 28), ctypes.byref(sz), None)
+    assert st == 0 and not offs.any()
