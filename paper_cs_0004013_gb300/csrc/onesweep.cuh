@@ -17,12 +17,13 @@
 // ticket so that every predecessor of a tile is already running):
 //  1. load: warp w takes keys [w*32*ITEMS, (w+1)*32*ITEMS) of the tile,
 //     item j of lane l being key w*32*ITEMS + j*32 + l (coalesced);
-//  2. rank: per item, lanes with the same digit find each other with
-//     __match_any_sync; the highest such lane bumps the warp's private
-//     16-bit counter for the digit by the group size; a lane's rank within
-//     its warp is the counter before the bump plus the number of group
-//     lanes below it.  Warp-private counters keep the rank order equal to
-//     the input order (stability);
+//  2. rank: per item, lanes with the same digit find each other through a
+//     per-warp shared-memory table of lane masks (atomicOr, read back); the
+//     highest such lane bumps the warp's private 16-bit counter for the
+//     digit by the group size; a lane's rank within its warp is the counter
+//     before the bump plus the number of group lanes below it.
+//     Warp-private counters keep the rank order equal to the input order
+//     (stability);
 //  3. per digit: the tile's count (sum over warps) is published at once
 //     as an "aggregate" status word; the counters are rewritten as
 //     exclusive (digit, warp) prefixes, giving each key its position in the
@@ -97,9 +98,11 @@ struct OnesweepLayout {
   // threads doing the per-digit work, and digits per such thread
   static constexpr int DTH = DIGITS < THREADS ? DIGITS : THREADS;
   static constexpr int DPT = DIGITS / DTH;
-  static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;
+  static constexpr size_t MASK_BYTES = size_t(WARPS) * 256 * 4;  // per-warp lane-mask tables
+  static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;  // per-warp 16-bit digit counters
+  static constexpr size_t RANK_BYTES = MASK_BYTES + CNT_BYTES;
   static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
-  static constexpr size_t UNION_BYTES = ((CNT_BYTES > BUF_BYTES ? CNT_BYTES : BUF_BYTES) + 15) / 16 * 16;
+  static constexpr size_t UNION_BYTES = ((RANK_BYTES > BUF_BYTES ? RANK_BYTES : BUF_BYTES) + 15) / 16 * 16;
   static constexpr size_t OFF_GOFF = UNION_BYTES;
   static constexpr size_t OFF_WARP = OFF_GOFF + size_t(DIGITS) * 4;
   static constexpr size_t OFF_TILE = OFF_WARP + 32 * 4;
@@ -107,7 +110,8 @@ struct OnesweepLayout {
   static_assert(THREADS % 32 == 0 && THREADS <= 1024, "block shape");
   static_assert(TILE < 65536, "ranks are 16-bit");
   static_assert(DIGITS % DTH == 0, "digits must split evenly over threads");
-  static_assert((WARPS * DIGITS) % 8 == 0, "counter array is cleared in 16-byte units");
+  static_assert(RANK_BYTES % 16 == 0, "rank tables are cleared in 16-byte units");
+  static_assert(R >= 8 && R <= 13, "digits of 8 to 13 bits");
 };
 
 template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB>
@@ -116,8 +120,9 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   constexpr int DIGITS = L::DIGITS, WARPS = L::WARPS, TILE = L::TILE;
   constexpr int DTH = L::DTH, DPT = L::DPT;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem);  // [WARPS][DIGITS]
-  uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem);  // aliases s_cnt once ranks are final
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);                   // [WARPS][256]
+  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + L::MASK_BYTES);    // [WARPS][DIGITS]
+  uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem);  // aliases both once ranks are final
   uint32_t* s_goff = reinterpret_cast<uint32_t*>(smem + L::OFF_GOFF);
   uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L::OFF_WARP);
   uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
@@ -135,8 +140,8 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {
-    uint4* c4 = reinterpret_cast<uint4*>(s_cnt);
-    for (int i = tid; i < WARPS * DIGITS / 8; i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+    uint4* c4 = reinterpret_cast<uint4*>(smem);
+    for (int i = tid; i < int(L::RANK_BYTES / 16); i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   if (tid == 0) *s_tile = atomicAdd(a.tile_counter, 1u);
   __syncthreads();
@@ -162,23 +167,48 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
     }
   }
 
-  // 2. rank within the warp; ranks are < 2^16, two per register
+  // 2. rank within the warp; ranks are < 2^16, two per register.
+  // Lanes holding the same digit find each other through a per-warp table
+  // of lane masks indexed by the digit's low 8 bits (shared-memory atomicOr,
+  // then a read-back); digits wider than 8 bits split the remaining bits off
+  // with one ballot per bit.  The highest lane of a group advances the
+  // warp's counter for the digit; the highest lane touching a table slot
+  // clears it for the next item.  A warp whose 32 digits are all equal
+  // takes a shortcut without the table.
   uint16_t* wc = s_cnt + warp * DIGITS;
-  const uint32_t lt = lanemask_lt();
+  uint32_t* wm = s_mask + warp * 256;
+  const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
   uint32_t rk[(ITEMS + 1) / 2];
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t d = digit_of(key[j], a.shift, a.width);
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
-    const int leader = 31 - __clz(peers);
-    uint32_t before = 0;
-    if (lane == leader) {
-      before = wc[d];
-      wc[d] = uint16_t(before + __popc(peers));
+    uint32_t r;
+    if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
+      const uint32_t before = wc[d];
+      __syncwarp();
+      if (lane == 31) wc[d] = uint16_t(before + 32u);
+      __syncwarp();
+      r = before + lane;
+    } else {
+      const uint32_t lo = d & 255u;
+      uint32_t same_hi = 0xffffffffu;
+#pragma unroll
+      for (int b = 8; b < R; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t bl = __ballot_sync(0xffffffffu, bit);
+        same_hi &= bit ? bl : ~bl;
+      }
+      atomicOr(&wm[lo], 1u << lane);
+      __syncwarp();
+      const uint32_t slot = wm[lo];
+      const uint32_t peers = slot & same_hi;
+      const uint32_t before = wc[d];
+      __syncwarp();
+      if ((peers & gt) == 0) wc[d] = uint16_t(before + __popc(peers));
+      if ((slot & gt) == 0) wm[lo] = 0u;
+      __syncwarp();
+      r = before + __popc(peers & lt);
     }
-    __syncwarp();
-    before = __shfl_sync(0xffffffffu, before, leader);
-    const uint32_t r = before + __popc(peers & lt);
     if (j & 1) rk[j >> 1] |= r << 16;
     else rk[j >> 1] = r;
   }

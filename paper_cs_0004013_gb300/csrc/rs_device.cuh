@@ -21,6 +21,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+__device__ __forceinline__ uint32_t lanemask_gt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_gt;" : "=r"(m));
+  return m;
+}
+
 // Digit of `width` bits at `shift` (width >= 1, shift + width <= 32).
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t shift, uint32_t width) {
   uint32_t r;
