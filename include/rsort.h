@@ -64,7 +64,7 @@ typedef enum rs_status {
  *               RS_MODE_MSD = bucket by the top digit first, then sort each
  *               bucket locally (the bucketing + local sort pipeline of
  *               Sec. 3 / Sec. 4.6).
- *   tile:       index of the kernel tile shape (0 = automatic).            */
+ *   tile:       1 + index of the kernel tile shape (0 = automatic).         */
 enum { RS_MODE_AUTO = 0, RS_MODE_LSD = 1, RS_MODE_MSD = 2 };
 typedef struct rs_plan {
   uint32_t digit_bits;

@@ -137,7 +137,12 @@ struct SortPlan {
   size_t num_tiles = 0;
 };
 
-int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 11; }
+// Defaults from measurement on GB300 at n = 2^26 (uniform 31-bit keys):
+// 8-bit digits beat 11-bit ones because the 11-bit lookback walks 2048
+// status words per tile; the bigger 1024 x 16 tile wins for keys, the
+// 512 x 16 tile for pairs (which need twice the staging memory).
+int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 8; }
+uint32_t default_tile(int R, bool pairs) { return R == 8 ? (pairs ? 1u : 4u) : (pairs ? 1u : 4u); }
 
 // n + one tile must fit the 30-bit count field of 32-bit status words.
 bool needs_wide_status(uint64_t n) { return n + 65536 > uint64_t(StatusCodec<uint32_t>::kVal); }
@@ -145,27 +150,17 @@ bool needs_wide_status(uint64_t n) { return n + 65536 > uint64_t(StatusCodec<uin
 rs_status pick_kernel(int R, uint32_t tile_idx, bool pairs, bool wide, const OnesweepKernel** out) {
   int cnt = 0;
   const OnesweepKernel* ks = R == 8 ? onesweep_kernels_r8(&cnt) : onesweep_kernels_r11(&cnt);
-  // distinct tile shapes in registry order; shape 0 is the default
-  int shapes[16][2];
-  int ns = 0;
-  for (int i = 0; i < cnt && ns < 16; ++i) {
-    bool seen = false;
-    for (int s = 0; s < ns; ++s) seen |= (shapes[s][0] == ks[i].threads && shapes[s][1] == ks[i].items);
-    if (!seen) {
-      shapes[ns][0] = ks[i].threads;
-      shapes[ns][1] = ks[i].items;
-      ++ns;
-    }
-  }
-  const uint32_t t = tile_idx == 0 ? 0 : tile_idx - 1;
-  if (t >= uint32_t(ns)) return fail(RS_ERR_UNSUPPORTED, "tile shape %u not available for %d-bit digits", tile_idx, R);
+  const int shape = tile_idx == 0 ? 0 : int(tile_idx) - 1;
+  bool any = false;
   for (int i = 0; i < cnt; ++i) {
-    if (ks[i].threads == shapes[t][0] && ks[i].items == shapes[t][1] && ks[i].pairs == pairs &&
-        ks[i].wide_status == wide) {
+    if (ks[i].shape != shape) continue;
+    any = true;
+    if (ks[i].pairs == pairs && ks[i].wide_status == wide) {
       *out = &ks[i];
       return RS_OK;
     }
   }
+  if (!any) return fail(RS_ERR_UNSUPPORTED, "tile shape %u not available for %d-bit digits", tile_idx, R);
   return fail(RS_ERR_UNSUPPORTED, "tile shape %u has no %s-status kernel (n too large for it)", tile_idx,
               wide ? "64-bit" : "32-bit");
 }
@@ -182,7 +177,10 @@ rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p) {
     p->dig[p->nd].width = (32 - s) < bits ? (32 - s) : bits;
     ++p->nd;
   }
-  rs_status st = pick_kernel(p->R, user ? user->tile : 0, pairs, needs_wide_status(n), &p->k);
+  const bool wide = needs_wide_status(n);
+  uint32_t tile = (user && user->tile) ? user->tile : default_tile(p->R, pairs);
+  if (wide && !(user && user->tile)) tile = 1;  // only shape 0 has 64-bit status kernels
+  rs_status st = pick_kernel(p->R, tile, pairs, wide, &p->k);
   if (st != RS_OK) return st;
   p->num_tiles = (n + p->k->tile - 1) / p->k->tile;
   return RS_OK;

@@ -28,10 +28,11 @@
 //     as an "aggregate" status word; the counters are rewritten as
 //     exclusive (digit, warp) prefixes, giving each key its position in the
 //     digit-sorted tile;
-//  4. stage keys (and values) in shared memory at their tile positions;
-//  5. lookback: walk back over earlier tiles' status words, a window of
+//  4. lookback: walk back over earlier tiles' status words, a window of
 //     them per round, adding aggregates until an "inclusive" word, then
 //     publish this tile's inclusive count; waits are bounded;
+//  5. stage keys (and values) in shared memory at their tile positions
+//     (the lookback may also run after this step: EARLY_LB = false);
 //  6. write the staged keys out in tile order, each to base[digit] + (keys
 //     of the digit in earlier tiles) + (position within the digit here).
 #pragma once
@@ -98,8 +99,10 @@ struct OnesweepLayout {
   // threads doing the per-digit work, and digits per such thread
   static constexpr int DTH = DIGITS < THREADS ? DIGITS : THREADS;
   static constexpr int DPT = DIGITS / DTH;
-  static constexpr size_t MASK_BYTES = size_t(WARPS) * 256 * 4;  // per-warp lane-mask tables
-  static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;  // per-warp 16-bit digit counters
+  // per-warp lane-mask table on the digit's low 8 bits, then per-warp
+  // 16-bit running counters per digit
+  static constexpr size_t MASK_BYTES = size_t(WARPS) * 256 * 4;
+  static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;
   static constexpr size_t RANK_BYTES = MASK_BYTES + CNT_BYTES;
   static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
   static constexpr size_t UNION_BYTES = ((RANK_BYTES > BUF_BYTES ? RANK_BYTES : BUF_BYTES) + 15) / 16 * 16;
@@ -114,15 +117,134 @@ struct OnesweepLayout {
   static_assert(R >= 8 && R <= 13, "digits of 8 to 13 bits");
 };
 
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB>
+// Vector relaxed load of 4 consecutive 32-bit status words (each word is
+// read single-copy atomically; the four need not be read together).
+__device__ __forceinline__ uint4 ld_relaxed4(const uint32_t* p) {
+  uint4 v;
+  asm volatile("ld.relaxed.gpu.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p)
+               : "memory");
+  return v;
+}
+
+// Exclusive prefix, over all earlier tiles, of the counts of this thread's
+// DPT digits d0 .. d0+DPT-1 (decoupled lookback).  Reads a window of LB
+// predecessors per round (LB * DPT loads in flight per thread).  Waits on a predecessor that has not published
+// are bounded (kSpinLimit rounds), after which the error word is raised.
+template <int DIGITS, int DPT, typename S, int LB>
+__device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uint32_t parity, uint32_t* err,
+                                         uint32_t (&prefix)[DPT]) {
+#pragma unroll
+  for (int k = 0; k < DPT; ++k) prefix[k] = 0;
+  if (tile == 0) return;
+  constexpr bool VEC = (sizeof(S) == 4) && (DPT % 4 == 0);
+  uint32_t spins = 0;
+  if constexpr (VEC) {
+    // one cursor for all DPT digits: rows are published whole, so the
+    // digits of a thread move back together
+    constexpr int NV = DPT / 4;
+    int nr[DPT];  // next row each digit still has to add
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) nr[k] = int(tile) - 1;
+    uint32_t pending = (DPT >= 32) ? 0xffffffffu : ((1u << DPT) - 1u);
+    while (pending) {
+      int c = -1;
+#pragma unroll
+      for (int k = 0; k < DPT; ++k)
+        if (pending & (1u << k)) c = nr[k] > c ? nr[k] : c;
+      uint4 w[LB][NV];
+#pragma unroll
+      for (int i = 0; i < LB; ++i)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+          if (c - i >= 0) w[i][v] = ld_relaxed4(reinterpret_cast<const uint32_t*>(st) + size_t(c - i) * DIGITS + d0 + 4 * v);
+      bool stalled = false;
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) {
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+          if (!(pending & (1u << k)) || nr[k] != c - i) continue;  // not this digit's next row
+          if (c - i < 0) break;
+          const uint4 q = w[i][k / 4];
+          const uint32_t x = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
+          if (!status_ready<S>(S(x), parity)) {
+            stalled = true;
+            continue;
+          }
+          prefix[k] += status_count<S>(S(x));
+          if (status_inclusive<S>(S(x))) pending &= ~(1u << k);
+          else --nr[k];
+        }
+        if ((pending & (1u << k)) && nr[k] < 0) {  // cannot happen: tile 0 is always inclusive
+          pending &= ~(1u << k);
+          atomicOr(err, kErrTimeout);
+        }
+      }
+      if (pending && stalled) {
+        if (++spins > kSpinLimit) {
+          atomicOr(err, kErrTimeout);
+          return;
+        }
+        if (spins > 16) __nanosleep(100);
+      }
+    }
+  } else {
+    int pred[DPT];
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) pred[k] = int(tile) - 1;
+    uint32_t pending = (1u << DPT) - 1u;
+    while (pending) {
+      S w[DPT][LB];
+#pragma unroll
+      for (int k = 0; k < DPT; ++k)
+#pragma unroll
+        for (int i = 0; i < LB; ++i)
+          if ((pending & (1u << k)) && pred[k] - i >= 0) w[k][i] = ld_relaxed(st + size_t(pred[k] - i) * DIGITS + d0 + k);
+      bool stalled = false;
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) {
+        if (!(pending & (1u << k))) continue;
+#pragma unroll
+        for (int i = 0; i < LB; ++i) {
+          if (!(pending & (1u << k))) break;
+          if (pred[k] < 0) {  // cannot happen: tile 0 is always inclusive
+            pending &= ~(1u << k);
+            atomicOr(err, kErrTimeout);
+            break;
+          }
+          const S x = w[k][i];
+          if (!status_ready<S>(x, parity)) {
+            stalled = true;
+            break;
+          }
+          prefix[k] += status_count<S>(x);
+          if (status_inclusive<S>(x)) pending &= ~(1u << k);
+          else --pred[k];
+        }
+      }
+      if (pending && stalled) {
+        if (++spins > kSpinLimit) {
+          atomicOr(err, kErrTimeout);
+          return;
+        }
+        if (spins > 16) __nanosleep(100);
+      }
+    }
+  }
+}
+
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
 __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs a) {
   using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
   constexpr int DIGITS = L::DIGITS, WARPS = L::WARPS, TILE = L::TILE;
   constexpr int DTH = L::DTH, DPT = L::DPT;
   extern __shared__ __align__(16) unsigned char smem[];
-  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);                   // [WARPS][256]
-  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + L::MASK_BYTES);    // [WARPS][DIGITS]
-  uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem);  // aliases both once ranks are final
+  // rank tables ([WARPS][256] lane masks, then [WARPS][DIGITS] 16-bit
+  // counters), aliased by the staging buffer once positions are final
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + L::MASK_BYTES);
+  uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_goff = reinterpret_cast<uint32_t*>(smem + L::OFF_GOFF);
   uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L::OFF_WARP);
   uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
@@ -169,101 +291,130 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
 
   // 2. rank within the warp; ranks are < 2^16, two per register.
   // Lanes holding the same digit find each other through a per-warp table
-  // of lane masks indexed by the digit's low 8 bits (shared-memory atomicOr,
-  // then a read-back); digits wider than 8 bits split the remaining bits off
+  // of lane masks (shared-memory atomicOr, then a read-back); digits wider
+  // than 8 bits index the table by their low 8 bits and split the rest off
   // with one ballot per bit.  The highest lane of a group advances the
-  // warp's counter for the digit; the highest lane touching a table slot
-  // clears it for the next item.  A warp whose 32 digits are all equal
-  // takes a shortcut without the table.
-  uint16_t* wc = s_cnt + warp * DIGITS;
-  uint32_t* wm = s_mask + warp * 256;
+  // warp's running count for the digit and clears the table slot.  A warp
+  // whose 32 digits are all equal takes a shortcut without the table.
   const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
   uint32_t rk[(ITEMS + 1) / 2];
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const uint32_t d = digit_of(key[j], a.shift, a.width);
     uint32_t r;
-    if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
-      const uint32_t before = wc[d];
-      __syncwarp();
-      if (lane == 31) wc[d] = uint16_t(before + 32u);
-      __syncwarp();
-      r = before + lane;
-    } else {
-      const uint32_t lo = d & 255u;
-      uint32_t same_hi = 0xffffffffu;
+    {
+      uint16_t* wc = s_cnt + warp * DIGITS;
+      uint32_t* wm = s_mask + warp * 256;
+      if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
+        const uint32_t before = wc[d];
+        __syncwarp();
+        if (lane == 31) wc[d] = uint16_t(before + 32u);
+        __syncwarp();
+        r = before + lane;
+      } else {
+        const uint32_t lo = d & 255u;
+        uint32_t same_hi = 0xffffffffu;
 #pragma unroll
-      for (int b = 8; b < R; ++b) {
-        const uint32_t bit = (d >> b) & 1u;
-        const uint32_t bl = __ballot_sync(0xffffffffu, bit);
-        same_hi &= bit ? bl : ~bl;
+        for (int b = 8; b < R; ++b) {
+          const uint32_t bit = (d >> b) & 1u;
+          const uint32_t bl = __ballot_sync(0xffffffffu, bit);
+          same_hi &= bit ? bl : ~bl;
+        }
+        atomicOr(&wm[lo], 1u << lane);
+        __syncwarp();
+        const uint32_t slot = wm[lo];
+        const uint32_t peers = slot & same_hi;
+        const uint32_t before = wc[d];
+        __syncwarp();
+        if ((peers & gt) == 0) wc[d] = uint16_t(before + __popc(peers));
+        if ((slot & gt) == 0) wm[lo] = 0u;
+        __syncwarp();
+        r = before + __popc(peers & lt);
       }
-      atomicOr(&wm[lo], 1u << lane);
-      __syncwarp();
-      const uint32_t slot = wm[lo];
-      const uint32_t peers = slot & same_hi;
-      const uint32_t before = wc[d];
-      __syncwarp();
-      if ((peers & gt) == 0) wc[d] = uint16_t(before + __popc(peers));
-      if ((slot & gt) == 0) wm[lo] = 0u;
-      __syncwarp();
-      r = before + __popc(peers & lt);
     }
     if (j & 1) rk[j >> 1] |= r << 16;
     else rk[j >> 1] = r;
   }
   __syncthreads();
 
-  // 3. per-digit tile counts -> aggregate status; counters -> exclusive prefixes
+  // 3. per-digit tile counts -> aggregate status; counts -> exclusive
+  // (digit, warp) prefixes, i.e. where each warp's run of a digit starts
   const int d0 = tid * DPT;
   uint32_t tot[DPT], loff[DPT];
   uint32_t my_sum = 0;
+  S* const status = reinterpret_cast<S*>(a.status);
   if (tid < DTH) {
-    CntVec<DPT> run;
-    run.zero();
+    {
+      CntVec<DPT> run;
+      run.zero();
 #pragma unroll 4
-    for (int wi = 0; wi < WARPS; ++wi) {
-      CntVec<DPT> v;
-      v.load(s_cnt + wi * DIGITS + d0);
-      run.add(v);
+      for (int wi = 0; wi < WARPS; ++wi) {
+        CntVec<DPT> v;
+        v.load(s_cnt + wi * DIGITS + d0);
+        run.add(v);
+      }
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) tot[k] = run.half(k);
     }
-    S* mine = reinterpret_cast<S*>(a.status) + size_t(tile) * DIGITS + d0;
+    S* mine = status + size_t(tile) * DIGITS + d0;
 #pragma unroll
     for (int k = 0; k < DPT; ++k) {
-      tot[k] = run.half(k);
       my_sum += tot[k];
       st_relaxed(mine + k, status_word<S>(route.parity, tile == 0, tot[k]));
     }
   }
   const uint32_t excl = block_exclusive_sum<THREADS>(my_sum, s_warp);
   if (tid < DTH) {
-    CntVec<DPT> run;
-    run.zero();
     uint32_t r = excl;
 #pragma unroll
     for (int k = 0; k < DPT; ++k) {
       loff[k] = r;
-      run.set_half(k, r);
       r += tot[k];
     }
+    {
+      CntVec<DPT> run;
+      run.zero();
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) run.set_half(k, loff[k]);
 #pragma unroll 4
-    for (int wi = 0; wi < WARPS; ++wi) {
-      CntVec<DPT> v;
-      v.load(s_cnt + wi * DIGITS + d0);
-      run.store(s_cnt + wi * DIGITS + d0);
-      run.add(v);
+      for (int wi = 0; wi < WARPS; ++wi) {
+        CntVec<DPT> v;
+        v.load(s_cnt + wi * DIGITS + d0);
+        run.store(s_cnt + wi * DIGITS + d0);
+        run.add(v);
+      }
     }
   }
+
+  // 4. chained scan over earlier tiles (decoupled lookback), either now or
+  // after the tile is staged
+  auto do_lookback = [&]() {
+    if (tid < DTH) {
+      uint32_t prefix[DPT];
+      // fewer loads in flight when keys and ranks are still live
+      constexpr int LBW = EARLY_LB ? ((8 / DPT) > 1 ? 8 / DPT : 1) : ((32 / DPT) > 1 ? 32 / DPT : 1);
+      lookback<DIGITS, DPT, S, LBW>(status, tile, d0, route.parity, a.err, prefix);
+      if (tile > 0) {
+        S* mine = status + size_t(tile) * DIGITS + d0;
+#pragma unroll
+        for (int k = 0; k < DPT; ++k) st_relaxed(mine + k, status_word<S>(route.parity, true, prefix[k] + tot[k]));
+      }
+#pragma unroll
+      for (int k = 0; k < DPT; ++k) s_goff[d0 + k] = a.bases[d0 + k] + prefix[k] - loff[k];
+    }
+  };
+  if constexpr (EARLY_LB) do_lookback();
   __syncthreads();
 
-  // 4. tile positions; stage the tile in shared memory in digit order
+  // 5. tile positions; stage the tile in shared memory in digit order
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
-    const uint32_t pos = s_cnt[warp * DIGITS + digit_of(key[j], a.shift, a.width)];
+    const uint32_t d = digit_of(key[j], a.shift, a.width);
+    const uint32_t pos = s_cnt[warp * DIGITS + d];
     if (j & 1) rk[j >> 1] += pos << 16;
     else rk[j >> 1] += pos;
   }
-  __syncthreads();  // counters are dead; the staging buffer reuses them
+  __syncthreads();  // rank tables are dead; the staging buffer reuses them
   uint32_t val[PAIRS ? ITEMS : 1];
   if constexpr (PAIRS) {
     if (valid == TILE) {
@@ -283,77 +434,17 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) s_buf[TILE + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = val[j];
   }
-
-  // 5. chained scan over earlier tiles (decoupled lookback).  Each round
-  // reads a window of LB predecessors per digit at once, then adds
-  // aggregates from the nearest one back to the first inclusive word.
-  if (tid < DTH) {
-    constexpr int LB = (16 / DPT) > 1 ? (16 / DPT) : 1;
-    uint32_t prefix[DPT];
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) prefix[k] = 0;
-    if (tile > 0) {
-      const S* st = reinterpret_cast<const S*>(a.status);
-      int pred[DPT];
-#pragma unroll
-      for (int k = 0; k < DPT; ++k) pred[k] = int(tile) - 1;
-      uint32_t pending = (1u << DPT) - 1u;
-      uint32_t spins = 0;
-      while (pending) {
-        S w[DPT][LB];
-#pragma unroll
-        for (int k = 0; k < DPT; ++k)
-#pragma unroll
-          for (int i = 0; i < LB; ++i)
-            if ((pending & (1u << k)) && pred[k] - i >= 0)
-              w[k][i] = ld_relaxed(st + size_t(pred[k] - i) * DIGITS + d0 + k);
-        bool stalled = false;
-#pragma unroll
-        for (int k = 0; k < DPT; ++k) {
-          if (!(pending & (1u << k))) continue;
-#pragma unroll
-          for (int i = 0; i < LB; ++i) {
-            if (!(pending & (1u << k))) break;
-            if (pred[k] < 0) {  // cannot happen: tile 0 is always inclusive
-              pending &= ~(1u << k);
-              atomicOr(a.err, kErrTimeout);
-              break;
-            }
-            const S x = w[k][i];
-            if (!status_ready<S>(x, route.parity)) {
-              stalled = true;
-              break;
-            }
-            prefix[k] += status_count<S>(x);
-            if (status_inclusive<S>(x)) pending &= ~(1u << k);
-            else --pred[k];
-          }
-        }
-        if (pending && stalled) {
-          if (++spins > kSpinLimit) {
-            atomicOr(a.err, kErrTimeout);
-            break;
-          }
-          if (spins > 16) __nanosleep(100);
-        }
-      }
-      S* mine = reinterpret_cast<S*>(a.status) + size_t(tile) * DIGITS + d0;
-#pragma unroll
-      for (int k = 0; k < DPT; ++k) st_relaxed(mine + k, status_word<S>(route.parity, true, prefix[k] + tot[k]));
-    }
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) s_goff[d0 + k] = a.bases[d0 + k] + prefix[k] - loff[k];
-  }
+  if constexpr (!EARLY_LB) do_lookback();
   __syncthreads();
 
   // 6. write out in tile order: runs of one digit go to consecutive
   // addresses.  The range check only guards against a corrupted offset (it
   // raises an error bit instead of writing out of bounds).
-  if (valid == TILE) {
-    bool oob = false;
+  bool oob = false;
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const uint32_t i = k * THREADS + tid;
+  for (int k = 0; k < ITEMS; ++k) {
+    const uint32_t i = k * THREADS + tid;
+    if (valid == TILE || i < valid) {
       const uint32_t kk = s_buf[i];
       const uint32_t g = s_goff[digit_of(kk, a.shift, a.width)] + i;
       if (g < a.n) {
@@ -363,46 +454,30 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
         oob = true;
       }
     }
-    if (oob) atomicOr(a.err, kErrBounds);
-  } else {
-    bool oob = false;
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const uint32_t i = k * THREADS + tid;
-      if (i < valid) {
-        const uint32_t kk = s_buf[i];
-        const uint32_t g = s_goff[digit_of(kk, a.shift, a.width)] + i;
-        if (g < a.n) {
-          kout[g] = kk;
-          if constexpr (PAIRS) vout[g] = s_buf[TILE + i];
-        } else {
-          oob = true;
-        }
-      }
-    }
-    if (oob) atomicOr(a.err, kErrBounds);
   }
+  if (oob) atomicOr(a.err, kErrBounds);
 }
 
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB>
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
 cudaError_t launch_onesweep(const PassArgs& a, unsigned grid, cudaStream_t s) {
   using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
-  onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB><<<grid, THREADS, L::SMEM, s>>>(a);
+  onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB, EARLY_LB><<<grid, THREADS, L::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB>
-OnesweepKernel make_onesweep() {
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
+OnesweepKernel make_onesweep(int shape_id) {
   using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
   return OnesweepKernel{R,
+                        shape_id,
                         THREADS,
                         ITEMS,
                         L::TILE,
                         PAIRS,
                         sizeof(S) == 8,
                         L::SMEM,
-                        &launch_onesweep<R, THREADS, ITEMS, PAIRS, S, MINB>,
-                        reinterpret_cast<const void*>(&onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB>)};
+                        &launch_onesweep<R, THREADS, ITEMS, PAIRS, S, MINB, EARLY_LB>,
+                        reinterpret_cast<const void*>(&onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB, EARLY_LB>)};
 }
 
 }  // namespace rs

@@ -7,13 +7,14 @@ namespace rs {
 using S32 = uint32_t;
 using S64 = unsigned long long;
 
-// Tile shapes: index 0 is the default.  MINB is the number of resident
-// blocks per SM the register budget is sized for.
+// Shape 0 is the default.  MINB = resident blocks per SM the register budget
+// is sized for; the last flag puts the lookback before the staging step.
 static const OnesweepKernel kR11[] = {
-    make_onesweep<11, 512, 16, false, S32, 2>(), make_onesweep<11, 512, 16, true, S32, 2>(),
-    make_onesweep<11, 512, 16, false, S64, 2>(), make_onesweep<11, 512, 16, true, S64, 2>(),
-    make_onesweep<11, 256, 32, false, S32, 2>(), make_onesweep<11, 256, 32, true, S32, 2>(),
-    make_onesweep<11, 1024, 8, false, S32, 1>(), make_onesweep<11, 1024, 8, true, S32, 1>(),
+    make_onesweep<11, 1024, 16, false, S32, 1, false>(0), make_onesweep<11, 1024, 16, true, S32, 1, false>(0),
+    make_onesweep<11, 1024, 16, false, S64, 1, false>(0), make_onesweep<11, 1024, 16, true, S64, 1, false>(0),
+    make_onesweep<11, 1024, 16, false, S32, 1, true>(1),  make_onesweep<11, 1024, 16, true, S32, 1, true>(1),
+    make_onesweep<11, 512, 16, false, S32, 2, false>(2),  make_onesweep<11, 512, 16, true, S32, 2, false>(2),
+    make_onesweep<11, 1024, 24, false, S32, 1, false>(3), make_onesweep<11, 1024, 24, true, S32, 1, false>(3),
 };
 
 const OnesweepKernel* onesweep_kernels_r11(int* count) {

@@ -6,11 +6,15 @@ namespace rs {
 using S32 = uint32_t;
 using S64 = unsigned long long;
 
+// Shape 0 is the default.  MINB = resident blocks per SM the register budget
+// is sized for; the last flag puts the lookback before the staging step.
 static const OnesweepKernel kR8[] = {
-    make_onesweep<8, 512, 16, false, S32, 2>(), make_onesweep<8, 512, 16, true, S32, 2>(),
-    make_onesweep<8, 512, 16, false, S64, 2>(), make_onesweep<8, 512, 16, true, S64, 2>(),
-    make_onesweep<8, 256, 32, false, S32, 2>(), make_onesweep<8, 256, 32, true, S32, 2>(),
-    make_onesweep<8, 384, 20, false, S32, 2>(), make_onesweep<8, 384, 20, true, S32, 2>(),
+    make_onesweep<8, 512, 16, false, S32, 2, false>(0), make_onesweep<8, 512, 16, true, S32, 2, false>(0),
+    make_onesweep<8, 512, 16, false, S64, 2, false>(0), make_onesweep<8, 512, 16, true, S64, 2, false>(0),
+    make_onesweep<8, 512, 16, false, S32, 2, true>(1),  make_onesweep<8, 512, 16, true, S32, 2, true>(1),
+    make_onesweep<8, 512, 24, false, S32, 2, false>(2), make_onesweep<8, 512, 24, true, S32, 2, false>(2),
+    make_onesweep<8, 1024, 16, false, S32, 1, false>(3), make_onesweep<8, 1024, 16, true, S32, 1, false>(3),
+    make_onesweep<8, 384, 20, false, S32, 2, false>(4), make_onesweep<8, 384, 20, true, S32, 2, false>(4),
 };
 
 const OnesweepKernel* onesweep_kernels_r8(int* count) {

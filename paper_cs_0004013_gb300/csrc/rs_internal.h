@@ -53,6 +53,7 @@ struct PassArgs {
 
 struct OnesweepKernel {
   int radix_bits;
+  int shape;         // tile-shape index (0 = default) selected by rs_plan.tile - 1
   int threads;
   int items;
   int tile;          // keys per tile
