@@ -132,6 +132,31 @@ rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in,
                         uint32_t shift, uint32_t width, void* temp,
                         size_t* temp_bytes, rs_stream_t stream);
 
+/* ---- sorting without any device allocation ------------------------------ */
+
+/* Largest n accepted by rs_sort_u32_noalloc. */
+#define RS_NOALLOC_MAX_KEYS (1u << 20)
+
+/* The keys-only sort of rs_sort_u32 for callers that cannot allocate device
+ * memory: code inside a host program that owns every allocation and offers
+ * no allocator, latency-critical code that cannot afford cudaMalloc's
+ * possible device-wide synchronisation, code that must not hit
+ * out-of-memory once running.  No counterpart in the paper.
+ *
+ * The caller still owns keys_in and keys_out (device, n keys each) and
+ * h_part_offsets (host, num_parts + 1, may be NULL).  Scratch comes from a
+ * fixed array of about 4.5 MiB inside the library's device memory, reserved
+ * on every GPU that loads the library until the process exits; nothing is
+ * allocated or freed by the call.  n above RS_NOALLOC_MAX_KEYS is rejected
+ * with RS_ERR_INVALID before any work.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture.  All calls on a device share the array:
+ * calls whose work overlaps on the GPU (e.g. on two streams) race and must
+ * be serialised by the caller.  Results are identical to rs_sort_u32's.   */
+rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, uint64_t n,
+                              uint32_t num_parts, uint64_t* h_part_offsets,
+                              rs_stream_t stream);
+
 /* ---- errors ------------------------------------------------------------- */
 
 /* Message for the last error raised on the calling thread ("" if none). */

@@ -23,7 +23,7 @@ __all__ = [
     "RsError", "RsPlan", "lib", "LIBRARY_PATH",
     "rs_sort_u32", "rs_sort_u32_pairs", "rs_sort_u32_segmented", "rs_digit_histograms",
     "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_version", "rs_trace_enable",
-    "rs_trace_read",
+    "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS",
     "sort", "sort_pairs", "sort_segmented", "temp_bytes", "part_offsets",
     "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD",
 ]
@@ -31,6 +31,7 @@ __all__ = [
 STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_TEMP_TOO_SMALL", 3: "RS_ERR_CUDA",
                 4: "RS_ERR_TIMEOUT", 5: "RS_ERR_UNSUPPORTED"}
 RS_MODE_AUTO, RS_MODE_LSD, RS_MODE_MSD = 0, 1, 2
+RS_NOALLOC_MAX_KEYS = 1 << 20
 
 
 class RsError(RuntimeError):
@@ -66,6 +67,7 @@ _SIGS = {
     "rs_check_device_error": [_P],
     "rs_version": [],
     "rs_trace_enable": [ctypes.c_int],
+    "rs_sort_u32_noalloc": [_P, _P, _U64, _U32, _U64P, _P],
     "rs_trace_read": [ctypes.POINTER(RsTraceEntry), _U32, ctypes.POINTER(ctypes.c_uint32)],
 }
 
@@ -183,6 +185,17 @@ def rs_radix_pass(keys_in, vals_in, keys_out, vals_out, n: int, shift: int, widt
     _check(lib.rs_radix_pass(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n, shift, width,
                              tp, ctypes.byref(tb), _stream(stream) if temp is not None else None))
     return tb.value if temp is None else None
+
+
+def rs_sort_u32_noalloc(keys_in, keys_out, n: int, num_parts: int = 64, stream=None,
+                        want_offsets: bool = True):
+    """Calls rs_sort_u32_noalloc: the keys-only sort with the library's own
+    fixed scratch (no device allocation; n <= RS_NOALLOC_MAX_KEYS).  Returns
+    the partition offsets (numpy uint64[num_parts + 1]) or None."""
+    offs = np.zeros(num_parts + 1, dtype=np.uint64) if want_offsets else None
+    op = offs.ctypes.data_as(_U64P) if offs is not None else None
+    _check(lib.rs_sort_u32_noalloc(_ptr(keys_in), _ptr(keys_out), n, num_parts, op, _stream(stream)))
+    return offs
 
 
 def rs_check_device_error(stream=None) -> None:

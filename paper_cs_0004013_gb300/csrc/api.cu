@@ -353,6 +353,16 @@ __global__ void seg_part_offsets_kernel(const uint64_t* seg, uint32_t num_segs, 
 }
 
 }  // namespace
+
+void set_last_error(int /*status*/, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
 }  // namespace rs
 
 using namespace rs;

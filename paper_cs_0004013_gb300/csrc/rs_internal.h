@@ -78,6 +78,9 @@ struct ScanKernel {
   cudaError_t (*launch)(const ScanArgs&, unsigned grid, cudaStream_t);
 };
 
+// Sets the calling thread's message for rs_last_error() (printf format).
+void set_last_error(int status, const char* fmt, ...);
+
 // Registries (defined in the kernel translation units).
 const OnesweepKernel* onesweep_kernels_r8(int* count);
 const OnesweepKernel* onesweep_kernels_r11(int* count);
