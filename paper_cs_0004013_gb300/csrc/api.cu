@@ -70,6 +70,13 @@ rs_status device_state(DeviceState** out) {
       RS_CUDA(cudaFuncSetAttribute(h->func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
               "cudaFuncSetAttribute(hist)");
     }
+    const SegKernels* sk = seg_kernels();
+    const void* fn[6] = {sk->pass_keys, sk->pass_pairs, sk->tiny_keys, sk->tiny_pairs, sk->small_keys, sk->small_pairs};
+    const size_t sm[6] = {sk->pass_smem_keys,  sk->pass_smem_pairs,  sk->tiny_smem_keys,
+                          sk->tiny_smem_pairs, sk->small_smem_keys, sk->small_smem_pairs};
+    for (int i = 0; i < 6; ++i)
+      RS_CUDA(cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm[i])),
+              "cudaFuncSetAttribute(segmented)");
     st.ready = true;
   }
   *out = &st;
@@ -77,9 +84,13 @@ rs_status device_state(DeviceState** out) {
 }
 
 // ---- tracing -------------------------------------------------------------------
-enum TraceKind { T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_KINDS };
-const char* const kTraceNames[T_KINDS] = {"clear", "upfront_hist", "digit_scan", "onesweep_r8", "onesweep_r11",
-                                          "seg_part_offsets"};
+enum TraceKind {
+  T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_SEGPLAN, T_SEGHIST, T_SEGSCAN, T_SEGPASS, T_LOCAL,
+  T_KINDS
+};
+const char* const kTraceNames[T_KINDS] = {"clear",       "upfront_hist", "digit_scan", "onesweep_r8",
+                                          "onesweep_r11", "seg_part_offsets", "seg_plan", "seg_hist",
+                                          "seg_scan",    "seg_pass",     "local_sort"};
 struct TraceRec {
   int kind;
   double keys;
@@ -131,6 +142,7 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 // ---- plan -------------------------------------------------------------------
 struct SortPlan {
   int R = 11;
+  bool msd = false;  // top-digit bucketing pass, then the segmented pipeline per bucket
   int nd = 0;
   DigitSpec dig[kMaxDigits] = {};
   const OnesweepKernel* k = nullptr;
@@ -142,6 +154,9 @@ struct SortPlan {
 // status words per tile; the bigger 1024 x 16 tile wins for keys, the
 // 512 x 16 tile for pairs (which need twice the staging memory).
 int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 8; }
+// MSD when the 256 top-digit buckets of a uniform input fit the one-block
+// local sort (<= 16384 keys each), so that one tiled pass replaces four.
+uint32_t default_mode(uint64_t n, bool /*pairs*/) { return n <= (uint64_t(1) << 22) && n >= (uint64_t(1) << 16) ? RS_MODE_MSD : RS_MODE_LSD; }
 uint32_t default_tile(int R, bool pairs) { return R == 8 ? (pairs ? 1u : 4u) : (pairs ? 1u : 4u); }
 
 // n + one tile must fit the 30-bit count field of 32-bit status words.
@@ -168,8 +183,11 @@ rs_status pick_kernel(int R, uint32_t tile_idx, bool pairs, bool wide, const One
 rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p) {
   const uint32_t bits = (user && user->digit_bits) ? user->digit_bits : uint32_t(default_digit_bits(n, pairs));
   if (bits != 8 && bits != 11) return fail(RS_ERR_UNSUPPORTED, "digit_bits must be 8 or 11 (got %u)", bits);
-  if (user && user->mode == RS_MODE_MSD) return fail(RS_ERR_UNSUPPORTED, "MSD mode is not available yet");
   if (user && user->mode > RS_MODE_MSD) return fail(RS_ERR_INVALID, "unknown mode %u", user->mode);
+  const uint32_t mode = (user && user->mode) ? user->mode : (bits == 8 ? default_mode(n, pairs) : RS_MODE_LSD);
+  p->msd = mode == RS_MODE_MSD;
+  if (p->msd && bits != 8) return fail(RS_ERR_UNSUPPORTED, "the MSD plan uses 8-bit digits");
+  if (p->msd && needs_wide_status(n)) return fail(RS_ERR_UNSUPPORTED, "the MSD plan needs n < 2^30 - 2^16");
   p->R = int(bits);
   p->nd = 0;
   for (uint32_t s = 0; s < 32; s += bits) {
@@ -284,6 +302,139 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
   return RS_OK;
 }
 
+
+// ---- the segmented pipeline (device-planned) ---------------------------------
+// 8-bit digits over the low `nd` bytes of the keys; large segments go
+// through tiled passes src -> (alt | dst) ... -> dst, tiny and small ones
+// are sorted src -> dst in shared memory.
+struct SegLayout {
+  size_t counts = 0, seg_hist = 0, seg_bases = 0, large_seg = 0, tile_prefix = 0, small_seg = 0, tiny_seg = 0;
+  size_t status = 0, alt_k = 0, alt_v = 0, end = 0;
+  size_t memset_from = 0, memset_bytes = 0;  // counts + seg_hist
+  size_t tiles_ub = 0;
+};
+
+SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int nd, bool pairs) {
+  const SegKernels* sk = seg_kernels();
+  SegLayout L;
+  L.tiles_ub = size_t((total_n + sk->tile - 1) / sk->tile) + num_segs;
+  off = align_up(off);
+  L.counts = off;
+  L.memset_from = off;
+  off += align_up(size_t(kSegCountWords) * 4);
+  L.seg_hist = off;
+  off = align_up(off + size_t(num_segs) * nd * 256 * 4);
+  L.memset_bytes = off - L.memset_from;
+  L.seg_bases = off;
+  off = align_up(off + size_t(num_segs) * nd * 256 * 4);
+  L.large_seg = off;
+  off = align_up(off + size_t(num_segs) * 4);
+  L.tile_prefix = off;
+  off = align_up(off + (size_t(num_segs) + 1) * 4);
+  L.small_seg = off;
+  off = align_up(off + size_t(num_segs) * 4);
+  L.tiny_seg = off;
+  off = align_up(off + size_t(num_segs) * 4);
+  L.status = off;
+  off = align_up(off + L.tiles_ub * 256 * 4);
+  L.alt_k = off;
+  off = align_up(off + size_t(total_n) * 4);
+  if (pairs) {
+    L.alt_v = off;
+    off = align_up(off + size_t(total_n) * 4);
+  }
+  L.end = off;
+  return L;
+}
+
+rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t* kin, const uint32_t* vin,
+                        uint32_t* kout, uint32_t* vout, const uint64_t* seg_off, uint32_t num_segs, int nd,
+                        DeviceState* ds, cudaStream_t s) {
+  const SegKernels* sk = seg_kernels();
+  const bool pairs = vin != nullptr;
+  uint32_t* counts = reinterpret_cast<uint32_t*>(temp + L.counts);
+  const unsigned sms = unsigned(ds->num_sms);
+  auto cap = [](size_t want, size_t limit) { return unsigned(want < limit ? (want > 0 ? want : 1) : limit); };
+  RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp + L.memset_from, 0, L.memset_bytes, s); }),
+          "cudaMemsetAsync(segment counts)");
+  SegPlanArgs pa{seg_off,
+                 num_segs,
+                 sk->tiny_max,
+                 sk->small_max,
+                 sk->tile,
+                 reinterpret_cast<uint32_t*>(temp + L.large_seg),
+                 reinterpret_cast<uint32_t*>(temp + L.tile_prefix),
+                 reinterpret_cast<uint32_t*>(temp + L.small_seg),
+                 reinterpret_cast<uint32_t*>(temp + L.tiny_seg),
+                 counts};
+  RS_CUDA(traced(T_SEGPLAN, 0, s, [&] { return launch_seg_plan(pa, s); }), "launch seg_plan");
+  DigitSpec dig[kMaxDigits] = {};
+  for (int j = 0; j < nd; ++j) dig[j] = DigitSpec{uint32_t(8 * j), 8u};
+  SegHistArgs ha{};
+  ha.keys = kin;
+  ha.seg_off = seg_off;
+  ha.large_seg = pa.large_seg;
+  ha.tile_prefix = pa.tile_prefix;
+  ha.counts = counts;
+  ha.tile = sk->tile;
+  ha.num_digits = nd;
+  for (int j = 0; j < nd; ++j) ha.dig[j] = dig[j];
+  ha.seg_hist = reinterpret_cast<uint32_t*>(temp + L.seg_hist);
+  ha.status = reinterpret_cast<uint32_t*>(temp + L.status);
+  RS_CUDA(traced(T_SEGHIST, 0, s, [&] { return launch_seg_hist(ha, cap(L.tiles_ub, size_t(sms) * 4), s); }),
+          "launch seg_hist");
+  SegScanArgs sa{ha.seg_hist, reinterpret_cast<uint32_t*>(temp + L.seg_bases), counts, nd};
+  RS_CUDA(traced(T_SEGSCAN, 0, s, [&] { return launch_seg_scan(sa, cap(num_segs, size_t(sms) * 4), s); }),
+          "launch seg_scan");
+  uint32_t* alt_k = reinterpret_cast<uint32_t*>(temp + L.alt_k);
+  uint32_t* alt_v = pairs ? reinterpret_cast<uint32_t*>(temp + L.alt_v) : nullptr;
+  const uint32_t* src_k = kin;
+  const uint32_t* src_v = vin;
+  for (int p = 0; p < nd; ++p) {
+    const bool to_out = ((nd - 1 - p) % 2) == 0;
+    SegPassArgs ga{};
+    ga.kin = src_k;
+    ga.kout = to_out ? kout : alt_k;
+    ga.vin = src_v;
+    ga.vout = pairs ? (to_out ? vout : alt_v) : nullptr;
+    ga.seg_off = seg_off;
+    ga.large_seg = pa.large_seg;
+    ga.tile_prefix = pa.tile_prefix;
+    ga.counts = counts;
+    ga.seg_bases = sa.seg_bases;
+    ga.num_digits = nd;
+    ga.pass = p;
+    ga.shift = dig[p].shift;
+    ga.width = dig[p].width;
+    ga.status = ha.status;
+    ga.tile_counter = counts + SEG_TICKETS + p;
+    ga.parity = uint32_t(p & 1) ^ 1u;
+    ga.err = ds->err;
+    RS_CUDA(traced(T_SEGPASS, 0, s,
+                   [&] { return launch_seg_pass(ga, pairs, cap(L.tiles_ub, size_t(sms) * 2), s); }),
+            "launch seg_pass");
+    src_k = ga.kout;
+    src_v = ga.vout;
+  }
+  LocalArgs la{};
+  la.kin = kin;
+  la.kout = kout;
+  la.vin = vin;
+  la.vout = vout;
+  la.seg_off = seg_off;
+  la.num_digits = nd;
+  for (int j = 0; j < nd; ++j) la.dig[j] = dig[j];
+  la.list = pa.tiny_seg;
+  la.count = counts + SEG_NUM_TINY;
+  RS_CUDA(traced(T_LOCAL, 0, s, [&] { return launch_local_sort(la, false, pairs, cap(num_segs, size_t(sms) * 8), s); }),
+          "launch local_sort (tiny)");
+  la.list = pa.small_seg;
+  la.count = counts + SEG_NUM_SMALL;
+  RS_CUDA(traced(T_LOCAL, 0, s, [&] { return launch_local_sort(la, true, pairs, cap(num_segs, size_t(sms) * 2), s); }),
+          "launch local_sort (small)");
+  return RS_OK;
+}
+
 rs_status check_common(const void* keys_in, const void* keys_out, uint64_t n, void* temp, size_t* temp_bytes) {
   if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
   if (n >= (uint64_t(1) << 32)) return fail(RS_ERR_INVALID, "n = %llu: must be below 2^32", (unsigned long long)n);
@@ -296,6 +447,98 @@ rs_status check_common(const void* keys_in, const void* keys_out, uint64_t n, vo
   return RS_OK;
 }
 
+
+// ---- the MSD plan ---------------------------------------------------------------
+// upfront histogram + scans of all four bytes, one tiled pass on the top
+// byte (input -> bucket buffer), then the segmented pipeline on the 256
+// buckets over the three low bytes (bucket buffer -> output).
+struct MsdLayout {
+  Layout base;          // control, histograms, bases, status of the top-byte pass
+  size_t bk = 0, bv = 0;  // bucket buffers (keys, values)
+  size_t seg_off = 0;   // [257] uint64 bucket offsets
+  SegLayout seg;
+  size_t total = 0;
+};
+
+MsdLayout make_msd_layout(const SortPlan& p, uint64_t n, bool pairs) {
+  MsdLayout M;
+  SortPlan q = p;
+  q.nd = 1;  // no alternate buffer: the top-byte pass writes the bucket buffer
+  M.base = make_layout(q, n, pairs);
+  // make_layout sized histograms for one digit: widen to four
+  const size_t digits = 256;
+  size_t off = 0;
+  M.base.ctrl = off;
+  off += kAlign;
+  M.base.hist = off;
+  off = align_up(off + size_t(p.nd) * digits * 4);
+  M.base.memset_bytes = off;
+  M.base.bases = off;
+  off = align_up(off + size_t(p.nd) * digits * 4);
+  M.base.status = off;
+  off = align_up(off + M.base.status_bytes);
+  M.bk = off;
+  off = align_up(off + size_t(n) * 4);
+  if (pairs) {
+    M.bv = off;
+    off = align_up(off + size_t(n) * 4);
+  }
+  M.seg_off = off;
+  off = align_up(off + 257 * 8);
+  M.seg = make_seg_layout(off, 256, n, p.nd - 1, pairs);
+  M.total = M.seg.end;
+  return M;
+}
+
+rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in, const uint32_t* vals_in,
+                  uint32_t* keys_out, uint32_t* vals_out, uint32_t n, unsigned char* temp, DeviceState* ds,
+                  cudaStream_t s) {
+  const bool pairs = vals_in != nullptr;
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + M.base.ctrl);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(temp + M.base.hist);
+  uint32_t* bases = reinterpret_cast<uint32_t*>(temp + M.base.bases);
+  uint32_t* bk = reinterpret_cast<uint32_t*>(temp + M.bk);
+  uint32_t* bv = pairs ? reinterpret_cast<uint32_t*>(temp + M.bv) : nullptr;
+  uint64_t* seg_off = reinterpret_cast<uint64_t*>(temp + M.seg_off);
+  const int top = p.nd - 1;
+  RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, M.base.memset_bytes, s); }),
+          "cudaMemsetAsync(temp)");
+  HistArgs ha{};
+  ha.keys = keys_in;
+  ha.n = n;
+  ha.num_digits = 1;
+  ha.dig[0] = p.dig[top];
+  ha.hist = hist + size_t(top) * 256;
+  ha.zero_ptr = reinterpret_cast<uint4*>(temp + M.base.status);
+  ha.zero_vec4 = M.base.status_bytes / 16;
+  const size_t work = (size_t(n) + 4095) / 4096;
+  unsigned hgrid = unsigned(ds->num_sms) * 2;
+  if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
+  RS_CUDA(traced(T_HIST, n, s, [&] { return hist_kernel(8)->launch(ha, hgrid, s); }), "launch upfront_hist");
+  ScanArgs sa{hist + size_t(top) * 256, bases + size_t(top) * 256, nullptr, n};
+  RS_CUDA(traced(T_SCAN, 0, s, [&] { return scan_kernel(8)->launch(sa, 1u, s); }), "launch digit_scan");
+  PassArgs pa{};
+  pa.keys_in = keys_in;
+  pa.keys_out = bk;
+  pa.keys_alt = bk;
+  pa.vals_in = vals_in;
+  pa.vals_out = bv;
+  pa.vals_alt = bv;
+  pa.n = n;
+  pa.shift = p.dig[top].shift;
+  pa.width = p.dig[top].width;
+  pa.pass = 0;
+  pa.num_passes = 1;
+  pa.bases = bases + size_t(top) * 256;
+  pa.skip = nullptr;
+  pa.status = temp + M.base.status;
+  pa.tile_counter = ctrl;
+  pa.err = ds->err;
+  RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, unsigned(p.num_tiles), s); }), "launch onesweep (top)");
+  RS_CUDA(launch_bases_to_offsets(bases + size_t(top) * 256, 256, n, seg_off, s), "launch bucket offsets");
+  return run_segmented(M.seg, temp, bk, bv, keys_out, vals_out, seg_off, 256, p.nd - 1, ds, s);
+}
+
 rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                     uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets, const rs_plan* plan, void* temp,
                     size_t* temp_bytes, cudaStream_t s, bool pairs) {
@@ -306,7 +549,12 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   SortPlan p;
   st = make_plan(n, pairs, plan, &p);
   if (st != RS_OK) return st;
-  const Layout L = make_layout(p, n, pairs);
+  Layout L = make_layout(p, n, pairs);
+  MsdLayout M;
+  if (p.msd) {
+    M = make_msd_layout(p, n, pairs);
+    L.total = M.total;
+  }
   if (!temp) {
     *temp_bytes = L.total;
     return RS_OK;
@@ -336,6 +584,9 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   DeviceState* ds = nullptr;
   st = device_state(&ds);
   if (st != RS_OK) return st;
+  if (p.msd)
+    return run_msd(p, M, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
+                   static_cast<unsigned char*>(temp), ds, s);
   return run_lsd(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
                  static_cast<unsigned char*>(temp), false, ds, s);
 }
@@ -406,30 +657,30 @@ rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in
       if (m > max_seg) max_seg = m;
     }
   }
-  SortPlan p;
-  rs_status st = make_plan(max_seg, pairs, plan, &p);
-  if (st != RS_OK) return st;
-  const Layout L = make_layout(p, max_seg, pairs);
+  if (plan && plan->digit_bits && plan->digit_bits != 8)
+    return fail(RS_ERR_UNSUPPORTED, "the segmented sort uses 8-bit digits");
+  if (needs_wide_status(total_n)) return fail(RS_ERR_UNSUPPORTED, "the segmented sort needs total_n < 2^30 - 2^16");
+  (void)max_seg;
+  const SegLayout L = make_seg_layout(0, num_segs, total_n, 4, pairs);
   if (!temp) {
-    *temp_bytes = L.total;
+    *temp_bytes = L.end;
     return RS_OK;
   }
   if (reinterpret_cast<uintptr_t>(temp) % kAlign) return fail(RS_ERR_INVALID, "temp is not 256-byte aligned");
-  if (*temp_bytes < L.total) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, L.total);
+  if (*temp_bytes < L.end) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, L.end);
   if (total_n > 0 && (!keys_in || !keys_out || !d_seg_offsets))
     return fail(RS_ERR_INVALID, "NULL buffer");
   const size_t nb = size_t(total_n) * 4;
-  if (overlaps(keys_out, nb, keys_in, nb) || overlaps(keys_out, nb, temp, L.total) ||
+  if (overlaps(keys_out, nb, keys_in, nb) || overlaps(keys_out, nb, temp, L.end) ||
       (pairs && (overlaps(vals_out, nb, vals_in, nb) || overlaps(vals_out, nb, keys_out, nb) ||
-                 overlaps(vals_out, nb, keys_in, nb) || overlaps(vals_out, nb, temp, L.total) ||
+                 overlaps(vals_out, nb, keys_in, nb) || overlaps(vals_out, nb, temp, L.end) ||
                  overlaps(keys_out, nb, vals_in, nb))))
     return fail(RS_ERR_INVALID, "an output overlaps another buffer");
+  if (num_segs == 0) return RS_OK;
   DeviceState* ds = nullptr;
-  if (num_segs > 0) {
-    st = device_state(&ds);
-    if (st != RS_OK) return st;
-  }
-  if (d_part_offsets && num_segs > 0) {
+  rs_status st = device_state(&ds);
+  if (st != RS_OK) return st;
+  if (d_part_offsets) {
     const size_t cnt = size_t(num_segs) * (num_parts + 1);
     RS_CUDA(traced(T_SEGOFF, 0, s,
                    [&] {
@@ -439,18 +690,9 @@ rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in
                    }),
             "launch seg_part_offsets");
   }
-  for (uint32_t i = 0; i < num_segs; ++i) {
-    const uint64_t a = h_seg_offsets[i], m = h_seg_offsets[i + 1] - a;
-    if (m == 0) continue;
-    SortPlan ps;
-    st = make_plan(m, pairs, plan, &ps);
-    if (st != RS_OK) return st;
-    const Layout Ls = make_layout(ps, m, pairs);
-    st = run_lsd(ps, Ls, keys_in + a, pairs ? vals_in + a : nullptr, keys_out + a, pairs ? vals_out + a : nullptr,
-                 uint32_t(m), static_cast<unsigned char*>(temp), false, ds, s);
-    if (st != RS_OK) return st;
-  }
-  return RS_OK;
+  if (total_n == 0) return RS_OK;
+  return run_segmented(L, static_cast<unsigned char*>(temp), keys_in, pairs ? vals_in : nullptr, keys_out,
+                       pairs ? vals_out : nullptr, d_seg_offsets, num_segs, 4, ds, s);
 }
 
 rs_status rs_digit_histograms(const uint32_t* keys, uint64_t n, uint32_t digit_bits, uint32_t* d_hist,

@@ -128,16 +128,19 @@ __device__ __forceinline__ uint4 ld_relaxed4(const uint32_t* p) {
   return v;
 }
 
-// Exclusive prefix, over all earlier tiles, of the counts of this thread's
-// DPT digits d0 .. d0+DPT-1 (decoupled lookback).  Reads a window of LB
-// predecessors per round (LB * DPT loads in flight per thread).  Waits on a predecessor that has not published
-// are bounded (kSpinLimit rounds), after which the error word is raised.
+// Exclusive prefix, over the earlier tiles of the same segment (tiles
+// first .. tile-1), of the counts of this thread's DPT digits d0 ..
+// d0+DPT-1 (decoupled lookback).  Reads a window of LB predecessors per round
+// (LB * DPT loads in flight per thread).  Waits on a predecessor that has not
+// published are bounded (kSpinLimit rounds), after which the error word is
+// raised.
 template <int DIGITS, int DPT, typename S, int LB>
-__device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uint32_t parity, uint32_t* err,
-                                         uint32_t (&prefix)[DPT]) {
+__device__ __forceinline__ void lookback(const S* st, uint32_t tile, uint32_t first, int d0, uint32_t parity,
+                                         uint32_t* err, uint32_t (&prefix)[DPT]) {
 #pragma unroll
   for (int k = 0; k < DPT; ++k) prefix[k] = 0;
-  if (tile == 0) return;
+  if (tile == first) return;
+  const int lo = int(first);
   constexpr bool VEC = (sizeof(S) == 4) && (DPT % 4 == 0);
   uint32_t spins = 0;
   if constexpr (VEC) {
@@ -149,7 +152,7 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uin
     for (int k = 0; k < DPT; ++k) nr[k] = int(tile) - 1;
     uint32_t pending = (DPT >= 32) ? 0xffffffffu : ((1u << DPT) - 1u);
     while (pending) {
-      int c = -1;
+      int c = lo - 1;
 #pragma unroll
       for (int k = 0; k < DPT; ++k)
         if (pending & (1u << k)) c = nr[k] > c ? nr[k] : c;
@@ -158,14 +161,15 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uin
       for (int i = 0; i < LB; ++i)
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-          if (c - i >= 0) w[i][v] = ld_relaxed4(reinterpret_cast<const uint32_t*>(st) + size_t(c - i) * DIGITS + d0 + 4 * v);
+          if (c - i >= lo)
+            w[i][v] = ld_relaxed4(reinterpret_cast<const uint32_t*>(st) + size_t(c - i) * DIGITS + d0 + 4 * v);
       bool stalled = false;
 #pragma unroll
       for (int k = 0; k < DPT; ++k) {
 #pragma unroll
         for (int i = 0; i < LB; ++i) {
           if (!(pending & (1u << k)) || nr[k] != c - i) continue;  // not this digit's next row
-          if (c - i < 0) break;
+          if (c - i < lo) break;
           const uint4 q = w[i][k / 4];
           const uint32_t x = (k & 3) == 0 ? q.x : (k & 3) == 1 ? q.y : (k & 3) == 2 ? q.z : q.w;
           if (!status_ready<S>(S(x), parity)) {
@@ -176,7 +180,7 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uin
           if (status_inclusive<S>(S(x))) pending &= ~(1u << k);
           else --nr[k];
         }
-        if ((pending & (1u << k)) && nr[k] < 0) {  // cannot happen: tile 0 is always inclusive
+        if ((pending & (1u << k)) && nr[k] < lo) {  // cannot happen: the first tile is inclusive
           pending &= ~(1u << k);
           atomicOr(err, kErrTimeout);
         }
@@ -200,7 +204,7 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uin
       for (int k = 0; k < DPT; ++k)
 #pragma unroll
         for (int i = 0; i < LB; ++i)
-          if ((pending & (1u << k)) && pred[k] - i >= 0) w[k][i] = ld_relaxed(st + size_t(pred[k] - i) * DIGITS + d0 + k);
+          if ((pending & (1u << k)) && pred[k] - i >= lo) w[k][i] = ld_relaxed(st + size_t(pred[k] - i) * DIGITS + d0 + k);
       bool stalled = false;
 #pragma unroll
       for (int k = 0; k < DPT; ++k) {
@@ -208,7 +212,7 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uin
 #pragma unroll
         for (int i = 0; i < LB; ++i) {
           if (!(pending & (1u << k))) break;
-          if (pred[k] < 0) {  // cannot happen: tile 0 is always inclusive
+          if (pred[k] < lo) {  // cannot happen: the first tile is inclusive
             pending &= ~(1u << k);
             atomicOr(err, kErrTimeout);
             break;
@@ -234,12 +238,75 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, int d0, uin
   }
 }
 
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
-__global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs a) {
+// Stable rank of ITEMS keys per thread within their warp (item j of lane l
+// is the warp's key j*32 + l).  Lanes holding the same digit find each other
+// through the warp's table of lane masks (shared-memory atomicOr, then a
+// read-back); digits wider than 8 bits index the table by their low 8 bits
+// and split the rest off with one ballot per bit.  The highest lane of a
+// group advances the warp's running count for the digit and clears the
+// table slot.  A warp whose 32 digits are all equal skips the table.  Ranks
+// are < 2^16, two per register.  wm / wc: this warp's mask table (256
+// words, zero) and counters (2^R halfwords, zero on the first call).
+template <int R, int ITEMS>
+__device__ __forceinline__ void warp_rank(const uint32_t (&key)[ITEMS], uint32_t shift, uint32_t width, uint32_t* wm,
+                                          uint16_t* wc, uint32_t (&rk)[(ITEMS + 1) / 2]) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t d = digit_of(key[j], shift, width);
+    uint32_t r;
+    if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
+      const uint32_t before = wc[d];
+      __syncwarp();
+      if (lane == 31) wc[d] = uint16_t(before + 32u);
+      __syncwarp();
+      r = before + lane;
+    } else {
+      const uint32_t lo = d & 255u;
+      uint32_t same_hi = 0xffffffffu;
+#pragma unroll
+      for (int b = 8; b < R; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t bl = __ballot_sync(0xffffffffu, bit);
+        same_hi &= bit ? bl : ~bl;
+      }
+      atomicOr(&wm[lo], 1u << lane);
+      __syncwarp();
+      const uint32_t slot = wm[lo];
+      const uint32_t peers = slot & same_hi;
+      const uint32_t before = wc[d];
+      __syncwarp();
+      if ((peers & gt) == 0) wc[d] = uint16_t(before + __popc(peers));
+      if ((slot & gt) == 0) wm[lo] = 0u;
+      __syncwarp();
+      r = before + __popc(peers & lt);
+    }
+    if (j & 1) rk[j >> 1] |= r << 16;
+    else rk[j >> 1] = r;
+  }
+}
+
+// Where one tile's keys come from and go to.
+struct TileJob {
+  uint32_t tile;          // row of the tile in the status array
+  uint32_t first;         // first tile of the tile's segment (the lookback stops there)
+  size_t base;            // index of the tile's first key in the source array
+  uint32_t valid;         // keys in the tile (<= TILE)
+  uint32_t out_start;     // output index of the segment's first key
+  uint32_t out_end;       // output indexes must stay below this
+  const uint32_t* bases;  // [2^R]: the segment's keys with a smaller digit
+};
+
+// One tile of an LSD pass (steps 1-6 above).  The rank tables must be zero
+// on entry (the caller clears them and synchronises the block).
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, bool EARLY_LB>
+__device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t* kin, uint32_t* kout,
+                                              const uint32_t* vin, uint32_t* vout, uint32_t shift, uint32_t width,
+                                              S* status, uint32_t parity, uint32_t* err, unsigned char* smem) {
   using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
   constexpr int DIGITS = L::DIGITS, WARPS = L::WARPS, TILE = L::TILE;
   constexpr int DTH = L::DTH, DPT = L::DPT;
-  extern __shared__ __align__(16) unsigned char smem[];
   // rank tables ([WARPS][256] lane masks, then [WARPS][DIGITS] 16-bit
   // counters), aliased by the staging buffer once positions are final
   uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);
@@ -247,34 +314,13 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_goff = reinterpret_cast<uint32_t*>(smem + L::OFF_GOFF);
   uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L::OFF_WARP);
-  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
-
-  const Route route = route_of(a.skip, a.pass, a.num_passes);
-  if (!route.active) return;
-  const uint32_t* kin = route.src == BUF_IN ? a.keys_in : (route.src == BUF_OUT ? a.keys_out : a.keys_alt);
-  uint32_t* kout = route.dst == BUF_OUT ? a.keys_out : a.keys_alt;
-  const uint32_t* vin = nullptr;
-  uint32_t* vout = nullptr;
-  if constexpr (PAIRS) {
-    vin = route.src == BUF_IN ? a.vals_in : (route.src == BUF_OUT ? a.vals_out : a.vals_alt);
-    vout = route.dst == BUF_OUT ? a.vals_out : a.vals_alt;
-  }
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  {
-    uint4* c4 = reinterpret_cast<uint4*>(smem);
-    for (int i = tid; i < int(L::RANK_BYTES / 16); i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
-  }
-  if (tid == 0) *s_tile = atomicAdd(a.tile_counter, 1u);
-  __syncthreads();
-  const uint32_t tile = *s_tile;
-  const size_t tile_base = size_t(tile) * TILE;
-  const size_t left = size_t(a.n) - tile_base;
-  const uint32_t valid = left < size_t(TILE) ? uint32_t(left) : uint32_t(TILE);
+  const uint32_t tile = job.tile, valid = job.valid;
 
   // 1. load the keys
   uint32_t key[ITEMS];
-  const size_t wbase = tile_base + size_t(warp) * 32 * ITEMS + lane;
+  const size_t wbase = job.base + size_t(warp) * 32 * ITEMS + lane;
+  const size_t wend = job.base + valid;
   if (valid == TILE) {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) key[j] = ld_stream(kin + wbase + j * 32);
@@ -285,56 +331,13 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const size_t idx = wbase + j * 32;
-      key[j] = idx < a.n ? kin[idx] : 0xffffffffu;
+      key[j] = idx < wend ? kin[idx] : 0xffffffffu;
     }
   }
 
-  // 2. rank within the warp; ranks are < 2^16, two per register.
-  // Lanes holding the same digit find each other through a per-warp table
-  // of lane masks (shared-memory atomicOr, then a read-back); digits wider
-  // than 8 bits index the table by their low 8 bits and split the rest off
-  // with one ballot per bit.  The highest lane of a group advances the
-  // warp's running count for the digit and clears the table slot.  A warp
-  // whose 32 digits are all equal takes a shortcut without the table.
-  const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
+  // 2. rank within the warp
   uint32_t rk[(ITEMS + 1) / 2];
-#pragma unroll
-  for (int j = 0; j < ITEMS; ++j) {
-    const uint32_t d = digit_of(key[j], a.shift, a.width);
-    uint32_t r;
-    {
-      uint16_t* wc = s_cnt + warp * DIGITS;
-      uint32_t* wm = s_mask + warp * 256;
-      if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
-        const uint32_t before = wc[d];
-        __syncwarp();
-        if (lane == 31) wc[d] = uint16_t(before + 32u);
-        __syncwarp();
-        r = before + lane;
-      } else {
-        const uint32_t lo = d & 255u;
-        uint32_t same_hi = 0xffffffffu;
-#pragma unroll
-        for (int b = 8; b < R; ++b) {
-          const uint32_t bit = (d >> b) & 1u;
-          const uint32_t bl = __ballot_sync(0xffffffffu, bit);
-          same_hi &= bit ? bl : ~bl;
-        }
-        atomicOr(&wm[lo], 1u << lane);
-        __syncwarp();
-        const uint32_t slot = wm[lo];
-        const uint32_t peers = slot & same_hi;
-        const uint32_t before = wc[d];
-        __syncwarp();
-        if ((peers & gt) == 0) wc[d] = uint16_t(before + __popc(peers));
-        if ((slot & gt) == 0) wm[lo] = 0u;
-        __syncwarp();
-        r = before + __popc(peers & lt);
-      }
-    }
-    if (j & 1) rk[j >> 1] |= r << 16;
-    else rk[j >> 1] = r;
-  }
+  warp_rank<R, ITEMS>(key, shift, width, s_mask + warp * 256, s_cnt + warp * DIGITS, rk);
   __syncthreads();
 
   // 3. per-digit tile counts -> aggregate status; counts -> exclusive
@@ -342,25 +345,21 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   const int d0 = tid * DPT;
   uint32_t tot[DPT], loff[DPT];
   uint32_t my_sum = 0;
-  S* const status = reinterpret_cast<S*>(a.status);
   if (tid < DTH) {
-    {
-      CntVec<DPT> run;
-      run.zero();
+    CntVec<DPT> run;
+    run.zero();
 #pragma unroll 4
-      for (int wi = 0; wi < WARPS; ++wi) {
-        CntVec<DPT> v;
-        v.load(s_cnt + wi * DIGITS + d0);
-        run.add(v);
-      }
-#pragma unroll
-      for (int k = 0; k < DPT; ++k) tot[k] = run.half(k);
+    for (int wi = 0; wi < WARPS; ++wi) {
+      CntVec<DPT> v;
+      v.load(s_cnt + wi * DIGITS + d0);
+      run.add(v);
     }
     S* mine = status + size_t(tile) * DIGITS + d0;
 #pragma unroll
     for (int k = 0; k < DPT; ++k) {
+      tot[k] = run.half(k);
       my_sum += tot[k];
-      st_relaxed(mine + k, status_word<S>(route.parity, tile == 0, tot[k]));
+      st_relaxed(mine + k, status_word<S>(parity, tile == job.first, tot[k]));
     }
   }
   const uint32_t excl = block_exclusive_sum<THREADS>(my_sum, s_warp);
@@ -371,36 +370,34 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
       loff[k] = r;
       r += tot[k];
     }
-    {
-      CntVec<DPT> run;
-      run.zero();
+    CntVec<DPT> run;
+    run.zero();
 #pragma unroll
-      for (int k = 0; k < DPT; ++k) run.set_half(k, loff[k]);
+    for (int k = 0; k < DPT; ++k) run.set_half(k, loff[k]);
 #pragma unroll 4
-      for (int wi = 0; wi < WARPS; ++wi) {
-        CntVec<DPT> v;
-        v.load(s_cnt + wi * DIGITS + d0);
-        run.store(s_cnt + wi * DIGITS + d0);
-        run.add(v);
-      }
+    for (int wi = 0; wi < WARPS; ++wi) {
+      CntVec<DPT> v;
+      v.load(s_cnt + wi * DIGITS + d0);
+      run.store(s_cnt + wi * DIGITS + d0);
+      run.add(v);
     }
   }
 
-  // 4. chained scan over earlier tiles (decoupled lookback), either now or
-  // after the tile is staged
+  // 4. chained scan over the segment's earlier tiles (decoupled lookback),
+  // either now or after the tile is staged
   auto do_lookback = [&]() {
     if (tid < DTH) {
       uint32_t prefix[DPT];
       // fewer loads in flight when keys and ranks are still live
       constexpr int LBW = EARLY_LB ? ((8 / DPT) > 1 ? 8 / DPT : 1) : ((32 / DPT) > 1 ? 32 / DPT : 1);
-      lookback<DIGITS, DPT, S, LBW>(status, tile, d0, route.parity, a.err, prefix);
-      if (tile > 0) {
+      lookback<DIGITS, DPT, S, LBW>(status, tile, job.first, d0, parity, err, prefix);
+      if (tile != job.first) {
         S* mine = status + size_t(tile) * DIGITS + d0;
 #pragma unroll
-        for (int k = 0; k < DPT; ++k) st_relaxed(mine + k, status_word<S>(route.parity, true, prefix[k] + tot[k]));
+        for (int k = 0; k < DPT; ++k) st_relaxed(mine + k, status_word<S>(parity, true, prefix[k] + tot[k]));
       }
 #pragma unroll
-      for (int k = 0; k < DPT; ++k) s_goff[d0 + k] = a.bases[d0 + k] + prefix[k] - loff[k];
+      for (int k = 0; k < DPT; ++k) s_goff[d0 + k] = job.out_start + job.bases[d0 + k] + prefix[k] - loff[k];
     }
   };
   if constexpr (EARLY_LB) do_lookback();
@@ -409,8 +406,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   // 5. tile positions; stage the tile in shared memory in digit order
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
-    const uint32_t d = digit_of(key[j], a.shift, a.width);
-    const uint32_t pos = s_cnt[warp * DIGITS + d];
+    const uint32_t pos = s_cnt[warp * DIGITS + digit_of(key[j], shift, width)];
     if (j & 1) rk[j >> 1] += pos << 16;
     else rk[j >> 1] += pos;
   }
@@ -424,7 +420,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
 #pragma unroll
       for (int j = 0; j < ITEMS; ++j) {
         const size_t idx = wbase + j * 32;
-        val[j] = idx < a.n ? vin[idx] : 0u;
+        val[j] = idx < wend ? vin[idx] : 0u;
       }
     }
   }
@@ -446,8 +442,8 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
     const uint32_t i = k * THREADS + tid;
     if (valid == TILE || i < valid) {
       const uint32_t kk = s_buf[i];
-      const uint32_t g = s_goff[digit_of(kk, a.shift, a.width)] + i;
-      if (g < a.n) {
+      const uint32_t g = s_goff[digit_of(kk, shift, width)] + i;
+      if (g >= job.out_start && g < job.out_end) {
         kout[g] = kk;
         if constexpr (PAIRS) vout[g] = s_buf[TILE + i];
       } else {
@@ -455,7 +451,48 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
       }
     }
   }
-  if (oob) atomicOr(a.err, kErrBounds);
+  if (oob) atomicOr(err, kErrBounds);
+}
+
+// Clears the rank tables and takes the block's tile ticket.
+template <int R, int THREADS, int ITEMS, bool PAIRS>
+__device__ __forceinline__ uint32_t begin_tile(uint32_t* counter, unsigned char* smem) {
+  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
+  uint4* c4 = reinterpret_cast<uint4*>(smem);
+  for (int i = threadIdx.x; i < int(L::RANK_BYTES / 16); i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1u);
+  __syncthreads();
+  return *s_tile;
+}
+
+// The plain pass: tile i covers keys [i * TILE, (i + 1) * TILE) of one array.
+template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
+__global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs a) {
+  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Route route = route_of(a.skip, a.pass, a.num_passes);
+  if (!route.active) return;
+  const uint32_t* kin = route.src == BUF_IN ? a.keys_in : (route.src == BUF_OUT ? a.keys_out : a.keys_alt);
+  uint32_t* kout = route.dst == BUF_OUT ? a.keys_out : a.keys_alt;
+  const uint32_t* vin = nullptr;
+  uint32_t* vout = nullptr;
+  if constexpr (PAIRS) {
+    vin = route.src == BUF_IN ? a.vals_in : (route.src == BUF_OUT ? a.vals_out : a.vals_alt);
+    vout = route.dst == BUF_OUT ? a.vals_out : a.vals_alt;
+  }
+  const uint32_t tile = begin_tile<R, THREADS, ITEMS, PAIRS>(a.tile_counter, smem);
+  TileJob job;
+  job.tile = tile;
+  job.first = 0;
+  job.base = size_t(tile) * L::TILE;
+  const size_t left = size_t(a.n) - job.base;
+  job.valid = left < size_t(L::TILE) ? uint32_t(left) : uint32_t(L::TILE);
+  job.out_start = 0;
+  job.out_end = a.n;
+  job.bases = a.bases;
+  onesweep_tile<R, THREADS, ITEMS, PAIRS, S, EARLY_LB>(job, kin, kout, vin, vout, a.shift, a.width,
+                                                        reinterpret_cast<S*>(a.status), route.parity, a.err, smem);
 }
 
 template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>

@@ -78,6 +78,94 @@ struct ScanKernel {
   cudaError_t (*launch)(const ScanArgs&, unsigned grid, cudaStream_t);
 };
 
+// ---- segmented pipeline (segmented.cu) ---------------------------------------
+// Words of the device counts array written by seg_plan.
+enum : int { SEG_NUM_LARGE = 0, SEG_NUM_SMALL = 1, SEG_NUM_TINY = 2, SEG_NUM_TILES = 3, SEG_TICKETS = 4 };
+// counts[SEG_TICKETS + p] is the tile ticket of pass p; the array has
+// SEG_TICKETS + kMaxDigits words.
+constexpr int kSegCountWords = SEG_TICKETS + kMaxDigits;
+
+struct SegPlanArgs {
+  const uint64_t* seg_off;  // [num_segs + 1]
+  uint32_t num_segs;
+  uint32_t tiny_max, small_max, tile;
+  uint32_t* large_seg;      // [num_segs] ids of large segments
+  uint32_t* tile_prefix;    // [num_segs + 1] first tile of each large segment
+  uint32_t* small_seg;      // [num_segs]
+  uint32_t* tiny_seg;       // [num_segs]
+  uint32_t* counts;         // [kSegCountWords]
+};
+
+struct SegHistArgs {
+  const uint32_t* keys;
+  const uint64_t* seg_off;
+  const uint32_t* large_seg;
+  const uint32_t* tile_prefix;
+  const uint32_t* counts;
+  uint32_t tile;
+  int num_digits;
+  DigitSpec dig[kMaxDigits];
+  uint32_t* seg_hist;  // [num_large][num_digits][256], zeroed before the launch
+  uint32_t* status;    // [tiles][256]; each tile's row is cleared here
+};
+
+struct SegScanArgs {
+  const uint32_t* seg_hist;
+  uint32_t* seg_bases;  // same shape
+  const uint32_t* counts;
+  int num_digits;
+};
+
+struct SegPassArgs {
+  const uint32_t* kin;
+  uint32_t* kout;
+  const uint32_t* vin;
+  uint32_t* vout;
+  const uint64_t* seg_off;
+  const uint32_t* large_seg;
+  const uint32_t* tile_prefix;
+  const uint32_t* counts;
+  const uint32_t* seg_bases;
+  int num_digits, pass;
+  uint32_t shift, width;
+  uint32_t* status;
+  uint32_t* tile_counter;
+  uint32_t parity;
+  uint32_t* err;
+};
+
+struct LocalArgs {
+  const uint32_t* kin;
+  uint32_t* kout;
+  const uint32_t* vin;
+  uint32_t* vout;
+  const uint64_t* seg_off;
+  const uint32_t* list;   // segment ids
+  const uint32_t* count;  // device count of list entries
+  int num_digits;
+  DigitSpec dig[kMaxDigits];
+};
+
+struct SegKernels {
+  uint32_t tile, tiny_max, small_max;
+  size_t pass_smem_keys, pass_smem_pairs, tiny_smem_keys, tiny_smem_pairs, small_smem_keys, small_smem_pairs;
+  const void* pass_keys;
+  const void* pass_pairs;
+  const void* tiny_keys;
+  const void* tiny_pairs;
+  const void* small_keys;
+  const void* small_pairs;
+};
+
+const SegKernels* seg_kernels();
+cudaError_t launch_seg_plan(const SegPlanArgs& a, cudaStream_t s);
+cudaError_t launch_seg_hist(const SegHistArgs& a, unsigned grid, cudaStream_t s);
+cudaError_t launch_seg_scan(const SegScanArgs& a, unsigned grid, cudaStream_t s);
+cudaError_t launch_seg_pass(const SegPassArgs& a, bool pairs, unsigned grid, cudaStream_t s);
+cudaError_t launch_local_sort(const LocalArgs& a, bool small, bool pairs, unsigned grid, cudaStream_t s);
+cudaError_t launch_bases_to_offsets(const uint32_t* bases, uint32_t num, uint64_t n, uint64_t* seg_off,
+                                    cudaStream_t s);
+
 // Sets the calling thread's message for rs_last_error() (printf format).
 void set_last_error(int status, const char* fmt, ...);
 

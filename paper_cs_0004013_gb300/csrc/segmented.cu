@@ -1,0 +1,328 @@
+// Many independent sorts in one pipeline: the segments of a concatenated
+// array, planned on the device.
+//
+// Paper: each segment is sorted by the same radix distribution as a whole
+// array (Sec. 3.2, Sec. 3.3.1).  The split into small segments sorted
+// entirely inside one block and large ones sorted by tiled passes mirrors
+// the paper's two levels: bucketing into per-cell ranges, then a local
+// radix sort of each cell's data (Sec. 3, revised pipeline of Sec. 4.6).
+// The MSD plan uses the same pipeline on the buckets of the top digit.
+//
+// Launch sequence (all on one stream, sizes only known on the device are
+// handled by persistent grid-stride loops):
+//   seg_plan      one block: classify segments (empty / tiny / small /
+//                 large), list them, number the tiles of large segments;
+//   seg_hist      per large tile: digit histograms into the segment's
+//                 arrays; clears the tile's status row;
+//   seg_scan      per large segment and digit: exclusive scan;
+//   seg_pass x P  onesweep passes over the large tiles, lookback confined to
+//                 the tile's own segment;
+//   local_sort    one block per tiny / small segment: every digit sorted
+//                 in shared memory, written once.
+#include <cuda_runtime.h>
+
+#include "onesweep.cuh"
+#include "rs_device.cuh"
+#include "rs_internal.h"
+
+namespace rs {
+
+namespace {
+
+// ---------------------------------------------------------------- planning
+__global__ void __launch_bounds__(1024) seg_plan_kernel(const SegPlanArgs a) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_tot[4];
+  uint32_t carry_l = 0, carry_s = 0, carry_t = 0, carry_tiles = 0;
+  const uint32_t n_chunks = (a.num_segs + 1023u) / 1024u;
+  for (uint32_t c = 0; c < n_chunks; ++c) {
+    const uint32_t s = c * 1024u + threadIdx.x;
+    uint64_t m = 0;
+    if (s < a.num_segs) m = a.seg_off[s + 1] - a.seg_off[s];
+    const bool valid = s < a.num_segs && m > 0;
+    const bool tiny = valid && m <= a.tiny_max;
+    const bool small = valid && !tiny && m <= a.small_max;
+    const bool large = valid && m > a.small_max;
+    const uint32_t nt = large ? uint32_t((m + a.tile - 1) / a.tile) : 0u;
+    const uint32_t el = block_exclusive_sum<1024>(large ? 1u : 0u, s_warp, &s_tot[0]);
+    const uint32_t es = block_exclusive_sum<1024>(small ? 1u : 0u, s_warp, &s_tot[1]);
+    const uint32_t et = block_exclusive_sum<1024>(tiny ? 1u : 0u, s_warp, &s_tot[2]);
+    const uint32_t ex = block_exclusive_sum<1024>(nt, s_warp, &s_tot[3]);
+    if (large) {
+      a.large_seg[carry_l + el] = s;
+      a.tile_prefix[carry_l + el] = carry_tiles + ex;
+    }
+    if (small) a.small_seg[carry_s + es] = s;
+    if (tiny) a.tiny_seg[carry_t + et] = s;
+    carry_l += s_tot[0];
+    carry_s += s_tot[1];
+    carry_t += s_tot[2];
+    carry_tiles += s_tot[3];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    a.tile_prefix[carry_l] = carry_tiles;
+    a.counts[SEG_NUM_LARGE] = carry_l;
+    a.counts[SEG_NUM_SMALL] = carry_s;
+    a.counts[SEG_NUM_TINY] = carry_t;
+    a.counts[SEG_NUM_TILES] = carry_tiles;
+  }
+}
+
+// Index of the large segment holding large tile t (the last i with
+// tile_prefix[i] <= t).
+__device__ __forceinline__ uint32_t find_segment(const uint32_t* tile_prefix, uint32_t num_large, uint32_t t) {
+  uint32_t lo = 0, hi = num_large;  // invariant: tile_prefix[lo] <= t < tile_prefix[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (tile_prefix[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// -------------------------------------------------------------- histograms
+__global__ void __launch_bounds__(512) seg_hist_kernel(const SegHistArgs a) {
+  __shared__ uint32_t sh[kMaxDigits * 256];
+  __shared__ uint32_t s_seg[3];
+  const uint32_t num_large = a.counts[SEG_NUM_LARGE], total = a.counts[SEG_NUM_TILES];
+  const int nd = a.num_digits;
+  for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+    for (int i = threadIdx.x; i < nd * 256; i += 512) sh[i] = 0u;
+    if (threadIdx.x == 0) {
+      const uint32_t li = find_segment(a.tile_prefix, num_large, t);
+      const uint32_t s = a.large_seg[li];
+      s_seg[0] = li;
+      s_seg[1] = t - a.tile_prefix[li];
+      s_seg[2] = s;
+    }
+    __syncthreads();
+    const uint32_t li = s_seg[0];
+    const uint64_t seg_start = a.seg_off[s_seg[2]], seg_end = a.seg_off[s_seg[2] + 1];
+    const uint64_t start = seg_start + uint64_t(s_seg[1]) * a.tile;
+    const uint64_t end = start + a.tile < seg_end ? start + a.tile : seg_end;
+    for (uint64_t i = start + threadIdx.x; i < end; i += 512) {
+      const uint32_t k = ld_stream(a.keys + i);
+#pragma unroll
+      for (int j = 0; j < kMaxDigits; ++j)
+        if (j < nd) atomicAdd(&sh[j * 256 + digit_of(k, a.dig[j].shift, a.dig[j].width)], 1u);
+    }
+    // this tile's chained-scan status row starts out "not ready"
+    for (int i = threadIdx.x; i < 256; i += 512) a.status[size_t(t) * 256 + i] = 0u;
+    __syncthreads();
+    uint32_t* h = a.seg_hist + size_t(li) * nd * 256;
+    for (int i = threadIdx.x; i < nd * 256; i += 512)
+      if (sh[i]) atomicAdd(&h[i], sh[i]);
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(256) seg_scan_kernel(const SegScanArgs a) {
+  __shared__ uint32_t s_warp[32];
+  const uint32_t num_large = a.counts[SEG_NUM_LARGE];
+  for (uint32_t li = blockIdx.x; li < num_large; li += gridDim.x) {
+    for (int j = 0; j < a.num_digits; ++j) {
+      const size_t at = (size_t(li) * a.num_digits + j) * 256 + threadIdx.x;
+      const uint32_t v = a.seg_hist[at];
+      a.seg_bases[at] = block_exclusive_sum<256>(v, s_warp);
+    }
+  }
+}
+
+// ------------------------------------------------------------ tiled passes
+template <int THREADS, int ITEMS, bool PAIRS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) seg_pass_kernel(const SegPassArgs a) {
+  using L = OnesweepLayout<8, THREADS, ITEMS, PAIRS>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t num_large = a.counts[SEG_NUM_LARGE], total = a.counts[SEG_NUM_TILES];
+  for (;;) {
+    const uint32_t t = begin_tile<8, THREADS, ITEMS, PAIRS>(a.tile_counter, smem);
+    if (t >= total) return;  // uniform across the block
+    const uint32_t li = find_segment(a.tile_prefix, num_large, t);
+    const uint32_t s = a.large_seg[li];
+    const uint64_t seg_start = a.seg_off[s], seg_end = a.seg_off[s + 1];
+    TileJob job;
+    job.tile = t;
+    job.first = a.tile_prefix[li];
+    job.base = seg_start + size_t(t - job.first) * L::TILE;
+    const uint64_t left = seg_end - job.base;
+    job.valid = left < uint64_t(L::TILE) ? uint32_t(left) : uint32_t(L::TILE);
+    job.out_start = uint32_t(seg_start);
+    job.out_end = uint32_t(seg_end);
+    job.bases = a.seg_bases + (size_t(li) * a.num_digits + a.pass) * 256;
+    onesweep_tile<8, THREADS, ITEMS, PAIRS, uint32_t, false>(job, a.kin, a.kout, a.vin, a.vout, a.shift, a.width,
+                                                              a.status, a.parity, a.err, smem);
+    __syncthreads();  // the next tile reuses shared memory
+  }
+}
+
+// ------------------------------------------------------ one-block local sort
+template <int THREADS, int ITEMS, bool PAIRS>
+struct LocalLayout {
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr size_t MASK_BYTES = size_t(WARPS) * 256 * 4;
+  static constexpr size_t CNT_BYTES = size_t(WARPS) * 256 * 2;
+  static constexpr size_t OFF_BUF = MASK_BYTES + CNT_BYTES;
+  static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
+  static constexpr size_t OFF_WARP = OFF_BUF + BUF_BYTES;
+  static constexpr size_t SMEM = OFF_WARP + 32 * 4;
+  static_assert(THREADS >= 256, "one thread per 8-bit digit in the scan");
+  static_assert((MASK_BYTES + CNT_BYTES) % 16 == 0, "tables are cleared in 16-byte units");
+};
+
+// Sorts each listed segment (at most THREADS * ITEMS keys) by every digit
+// of the plan, least significant first, entirely in shared memory: per
+// digit a stable warp rank (the same lane-mask tables as the tiled pass),
+// per-digit tile offsets, and a scatter into the staging buffer, which the
+// next digit reads back.  Keys past the segment's end act as 0xFFFFFFFF and
+// stay behind every real key.  Writes src -> dst once.
+template <int THREADS, int ITEMS, bool PAIRS>
+__global__ void __launch_bounds__(THREADS, 1) local_sort_kernel(const LocalArgs a) {
+  using L = LocalLayout<THREADS, ITEMS, PAIRS>;
+  constexpr int TILE = L::TILE, WARPS = L::WARPS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + L::MASK_BYTES);
+  uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem + L::OFF_BUF);
+  uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L::OFF_WARP);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t count = *a.count;
+  for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
+    const uint32_t s = a.list[k];
+    const uint64_t start = a.seg_off[s];
+    const uint32_t m = uint32_t(a.seg_off[s + 1] - start);
+    uint32_t key[ITEMS], val[PAIRS ? ITEMS : 1];
+    const uint32_t wofs = uint32_t(warp) * 32 * ITEMS + lane;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t i = wofs + j * 32;
+      key[j] = i < m ? a.kin[start + i] : 0xffffffffu;
+      if constexpr (PAIRS) val[j] = i < m ? a.vin[start + i] : 0u;
+    }
+    for (int p = 0; p < a.num_digits; ++p) {
+      const uint32_t shift = a.dig[p].shift, width = a.dig[p].width;
+      uint4* c4 = reinterpret_cast<uint4*>(smem);
+      for (int i = tid; i < int(L::OFF_BUF / 16); i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+      __syncthreads();
+      uint32_t rk[(ITEMS + 1) / 2];
+      warp_rank<8, ITEMS>(key, shift, width, s_mask + warp * 256, s_cnt + warp * 256, rk);
+      __syncthreads();
+      // per digit (threads 0..255): total over warps, exclusive over digits,
+      // then exclusive (digit, warp) offsets
+      uint32_t tot = 0;
+      if (tid < 256)
+        for (int wi = 0; wi < WARPS; ++wi) tot += s_cnt[wi * 256 + tid];
+      const uint32_t excl = block_exclusive_sum<THREADS>(tid < 256 ? tot : 0u, s_warp);
+      if (tid < 256) {
+        uint32_t run = excl;
+        for (int wi = 0; wi < WARPS; ++wi) {
+          const uint32_t v = s_cnt[wi * 256 + tid];
+          s_cnt[wi * 256 + tid] = uint16_t(run);
+          run += v;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t pos = ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu) + s_cnt[warp * 256 + digit_of(key[j], shift, width)];
+        s_buf[pos] = key[j];
+        if constexpr (PAIRS) s_buf[TILE + pos] = val[j];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) {
+        key[j] = s_buf[wofs + j * 32];
+        if constexpr (PAIRS) val[j] = s_buf[TILE + wofs + j * 32];
+      }
+      __syncthreads();
+    }
+    // the staging buffer holds the sorted segment (then the padding)
+    for (uint32_t i = tid; i < m; i += THREADS) {
+      a.kout[start + i] = s_buf[i];
+      if constexpr (PAIRS) a.vout[start + i] = s_buf[TILE + i];
+    }
+    __syncthreads();
+  }
+}
+
+// Bucket offsets of an MSD plan: the exclusive scan of the top digit as
+// segment offsets (uint64), the last one being n.
+__global__ void bases_to_offsets_kernel(const uint32_t* bases, uint32_t num, uint64_t n, uint64_t* seg_off) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < num) seg_off[i] = bases[i];
+  if (i == num) seg_off[i] = n;
+}
+
+template <int THREADS, int ITEMS, bool PAIRS, int MINB>
+cudaError_t launch_seg_pass(const SegPassArgs& a, unsigned grid, cudaStream_t s) {
+  using L = OnesweepLayout<8, THREADS, ITEMS, PAIRS>;
+  seg_pass_kernel<THREADS, ITEMS, PAIRS, MINB><<<grid, THREADS, L::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int THREADS, int ITEMS, bool PAIRS>
+cudaError_t launch_local(const LocalArgs& a, unsigned grid, cudaStream_t s) {
+  using L = LocalLayout<THREADS, ITEMS, PAIRS>;
+  local_sort_kernel<THREADS, ITEMS, PAIRS><<<grid, THREADS, L::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Tiled passes over large segments: 8-bit digits, 512 x 16 tiles.
+constexpr int kSegThreads = 512, kSegItems = 16;
+// Local sorts: tiny segments <= 256 x 16 keys, small ones <= 1024 x 16 keys.
+constexpr int kTinyThreads = 256, kSmallThreads = 1024, kLocalItems = 16;
+
+const SegKernels* seg_kernels() {
+  static const SegKernels k = {
+      uint32_t(kSegThreads * kSegItems),
+      uint32_t(kTinyThreads * kLocalItems),
+      uint32_t(kSmallThreads * kLocalItems),
+      OnesweepLayout<8, kSegThreads, kSegItems, false>::SMEM,
+      OnesweepLayout<8, kSegThreads, kSegItems, true>::SMEM,
+      LocalLayout<kTinyThreads, kLocalItems, false>::SMEM,
+      LocalLayout<kTinyThreads, kLocalItems, true>::SMEM,
+      LocalLayout<kSmallThreads, kLocalItems, false>::SMEM,
+      LocalLayout<kSmallThreads, kLocalItems, true>::SMEM,
+      reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItems, false, 2>),
+      reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItems, true, 2>),
+      reinterpret_cast<const void*>(&local_sort_kernel<kTinyThreads, kLocalItems, false>),
+      reinterpret_cast<const void*>(&local_sort_kernel<kTinyThreads, kLocalItems, true>),
+      reinterpret_cast<const void*>(&local_sort_kernel<kSmallThreads, kLocalItems, false>),
+      reinterpret_cast<const void*>(&local_sort_kernel<kSmallThreads, kLocalItems, true>),
+  };
+  return &k;
+}
+
+cudaError_t launch_seg_plan(const SegPlanArgs& a, cudaStream_t s) {
+  seg_plan_kernel<<<1, 1024, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_seg_hist(const SegHistArgs& a, unsigned grid, cudaStream_t s) {
+  seg_hist_kernel<<<grid, 512, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_seg_scan(const SegScanArgs& a, unsigned grid, cudaStream_t s) {
+  seg_scan_kernel<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_seg_pass(const SegPassArgs& a, bool pairs, unsigned grid, cudaStream_t s) {
+  return pairs ? launch_seg_pass<kSegThreads, kSegItems, true, 2>(a, grid, s)
+               : launch_seg_pass<kSegThreads, kSegItems, false, 2>(a, grid, s);
+}
+cudaError_t launch_local_sort(const LocalArgs& a, bool small, bool pairs, unsigned grid, cudaStream_t s) {
+  if (small)
+    return pairs ? launch_local<kSmallThreads, kLocalItems, true>(a, grid, s)
+                 : launch_local<kSmallThreads, kLocalItems, false>(a, grid, s);
+  return pairs ? launch_local<kTinyThreads, kLocalItems, true>(a, grid, s)
+               : launch_local<kTinyThreads, kLocalItems, false>(a, grid, s);
+}
+cudaError_t launch_bases_to_offsets(const uint32_t* bases, uint32_t num, uint64_t n, uint64_t* seg_off,
+                                    cudaStream_t s) {
+  bases_to_offsets_kernel<<<(num + 256) / 256, 256, 0, s>>>(bases, num, n, seg_off);
+  return cudaGetLastError();
+}
+
+}  // namespace rs
