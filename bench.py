@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--pairs", action="store_true", help="time key+payload sorts as the main value")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["plain", "batched", "serve", "dist"], default="plain",
+                    help="plain: the headline 2^26 sort; batched: 4096 log-uniform segments in one call vs one "
+                         "call per array; serve: Poisson request stream; dist: the four skewed 2^26 inputs")
+    ap.add_argument("--requests", type=int, default=120, help="requests per load point (serve)")
     return ap.parse_args()
 
 
@@ -332,10 +336,208 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------- other workloads
+def _events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batched(args):
+    """Config 4: up to 4096 key+payload arrays, sizes log-uniform in
+    [2^10, 2^20], drawn until 2^28 keys; one rs_sort_u32_segmented call
+    (also replayed from a CUDA graph) vs one rs_sort_u32_pairs call per array."""
+    import torch
+    import synth
+    import paper_cs_0004013_gb300 as rs
+    torch.cuda.set_device(0)
+    keys, vals, offs = synth.segmented_batch(synth.CONFIG_SEED + 4)
+    n, S = keys.size, offs.size - 1
+    dk = torch.from_numpy(keys.view(np.int32)).cuda()
+    dv = torch.from_numpy(vals.view(np.int32)).cuda()
+    ko, vo = torch.empty_like(dk), torch.empty_like(dv)
+    d_off = torch.from_numpy(offs.view(np.int64)).cuda()
+    d_po = torch.empty(S * 65, dtype=torch.int64, device="cuda")
+    temp = torch.empty(rs.rs_sort_u32_segmented(None, dv, None, vo, None, offs, S, n, 64), dtype=torch.uint8,
+                       device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        rs.rs_sort_u32_segmented(dk, dv, ko, vo, d_off, offs, S, n, 64, d_po, None, temp, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        batched()
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    # correctness spot check against numpy on a few segments
+    for s_ in (0, S // 2, S - 1):
+        a, b = int(offs[s_]), int(offs[s_ + 1])
+        got = ko[a:b].cpu().numpy().view(np.uint32)
+        if not np.array_equal(got, np.sort(keys[a:b])):
+            raise SystemExit(f"batched output wrong in segment {s_}")
+    rs.rs_trace_read()
+    rs.rs_trace_enable(True)
+    e0, e1 = _events()
+    e0.record(stream)
+    for _ in range(args.steps):
+        batched()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rs.rs_trace_enable(False)
+    trace = rs.rs_trace_read()
+    t_batched = e0.elapsed_time(e1) / args.steps
+    # the same work captured once into a CUDA graph and replayed
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batched()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        rs.rs_sort_u32_segmented(dk, dv, ko, vo, d_off, offs, S, n, 64, d_po, None, temp, side)
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_graph = e0.elapsed_time(e1) / args.steps
+    # one plain call per array
+    big = int(np.diff(offs).max())
+    ptemp = torch.empty(rs.rs_sort_u32_pairs(None, None, None, None, big), dtype=torch.uint8, device="cuda")
+
+    def per_array():
+        for s_ in range(S):
+            a, b = int(offs[s_]), int(offs[s_ + 1])
+            rs.rs_sort_u32_pairs(dk[a:b], dv[a:b], ko[a:b], vo[a:b], b - a, 64, None, ptemp, stream,
+                                 want_offsets=True)
+
+    per_array()
+    torch.cuda.synchronize()
+    reps = max(1, args.steps // 5)
+    e0.record(stream)
+    for _ in range(reps):
+        per_array()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / reps
+    rs.rs_check_device_error()
+    val = n / (t_batched * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": val, "unit": "Gkeys/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": t_batched, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"batched segmented sort: {S} key+payload arrays, log-uniform sizes in "
+                                   f"[2^10, 2^20], {n} keys in total", "segments": int(S), "n": int(n)},
+            "graph_replay": {"value": n / (t_graph * 1e-3) / 1e9, "unit": "Gkeys/s", "ms_per_step": t_graph},
+            "per_array_plain": {"value": n / (t_plain * 1e-3) / 1e9, "unit": "Gkeys/s", "ms_per_step": t_plain,
+                                "calls_per_step": int(S)},
+            "speedup_vs_per_array": t_plain / t_batched,
+            "kernel_ms": {k: v["total_ms"] / v["launches"] for k, v in trace.items()}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Config 5: Poisson arrivals of sorts with sizes log-uniform in
+    [2^16, 2^26] (keys-only or pairs with probability 1/2), served with
+    continuous batching at 0.5x, 0.8x and 1.2x the measured serial capacity;
+    p50/p99 latency (arrival -> result on the host) and sustained keys/s."""
+    import torch
+    import synth
+    import paper_cs_0004013_gb300 as rs
+    from paper_cs_0004013_gb300.serve import Request, SortServer, latency_stats, serial_plain
+    torch.cuda.set_device(0)
+
+    def make(rate, seed):
+        out = []
+        for q in synth.serving_requests(args.requests, seed, rate_per_s=rate):
+            k = synth.uniform31(q["n"], q["seed"])
+            v = np.arange(q["n"], dtype=np.uint32) if q["pairs"] else None
+            out.append(Request.make(q["id"], q["arrival_s"], k, v))
+        return out
+
+    base = make(1.0, synth.CONFIG_SEED + 5)
+    total_keys = sum(r.n for r in base)
+    serial_plain(base)  # warm-up
+    t_serial = serial_plain(base)
+    serial_rate = total_keys / t_serial / 1e9
+    cap_req_s = len(base) / t_serial
+    srv = SortServer(slots=4, streams=4, mem_budget=24 << 30)
+    srv.run(make(1e9, synth.CONFIG_SEED + 5), realtime=False)  # warm-up (pools, kernels)
+    points = []
+    for load in (0.5, 0.8, 1.2):
+        reqs = make(cap_req_s * load, synth.CONFIG_SEED + 5)
+        srv.run(reqs, realtime=True)
+        rs.rs_check_device_error()
+        span = max(r.done_s for r in reqs) - min(r.arrival_s for r in reqs)
+        st = latency_stats(reqs)
+        st.update({"offered_load": load, "sustained_gkeys_s": total_keys / span / 1e9,
+                   "batches": len({r.batch for r in reqs})})
+        points.append(st)
+    # closed loop: everything arrives at once
+    reqs = make(1e9, synth.CONFIG_SEED + 5)
+    t0 = time.perf_counter()
+    srv.run(reqs, realtime=False)
+    t_closed = time.perf_counter() - t0
+    ok = all(np.array_equal(r.result()[0], np.sort(r.keys.numpy().view(np.uint32))) for r in reqs[:5])
+    if not ok:
+        raise SystemExit("served output differs from the sorted keys")
+    line = {"metric": METRIC, "value": total_keys / t_closed / 1e9, "unit": "Gkeys/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": t_closed * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"serving: {len(base)} requests, sizes log-uniform in [2^16, 2^26], half "
+                                   "key+payload; value = closed-loop keys/s including host<->device copies",
+                       "total_keys": int(total_keys)},
+            "serial_plain": {"value": serial_rate, "unit": "Gkeys/s", "seconds": t_serial},
+            "speedup_vs_serial": (total_keys / t_closed / 1e9) / serial_rate,
+            "load_points": points}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_dist(args):
+    """Config 3: 2^26 keys in the four skewed distributions, keys only."""
+    import torch
+    import synth
+    import paper_cs_0004013_gb300 as rs
+    torch.cuda.set_device(0)
+    res = {}
+    for dist in ("skewed_chunks", "few_distinct", "gauss_mix", "tight_clusters"):
+        keys = synth.config_keys(3, dist=dist)
+        d = torch.from_numpy(keys.view(np.int32)).cuda()
+        out = torch.empty_like(d)
+        temp = torch.empty(rs.rs_sort_u32(None, None, d.numel()), dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            rs.rs_sort_u32(d, out, d.numel(), 64, None, temp)
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(args.steps):
+            rs.rs_sort_u32(d, out, d.numel(), 64, None, temp)
+        e1.record()
+        torch.cuda.synchronize()
+        rs.rs_check_device_error()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[dist] = {"gkeys_s": d.numel() / ms / 1e6, "ms": ms}
+    line = {"metric": METRIC, "value": min(v["gkeys_s"] for v in res.values()), "unit": "Gkeys/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": 3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "2^26 keys, four skewed distributions, keys only; value = the slowest"},
+            "per_distribution": res}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serve":
+        return run_serve(args)
+    if args.workload == "dist":
+        return run_dist(args)
     return run_ours(args)
 
 

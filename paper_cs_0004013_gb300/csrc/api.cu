@@ -151,13 +151,13 @@ struct SortPlan {
 
 // Defaults from measurement on GB300 at n = 2^26 (uniform 31-bit keys):
 // 8-bit digits beat 11-bit ones because the 11-bit lookback walks 2048
-// status words per tile; the bigger 1024 x 16 tile wins for keys, the
-// 512 x 16 tile for pairs (which need twice the staging memory).
+// status words per tile; the 512 x 24 tile (shape 2) wins for keys, the
+// 512 x 16 tile (shape 0) for pairs (which need twice the staging memory).
 int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 8; }
 // MSD when the 256 top-digit buckets of a uniform input fit the one-block
 // local sort (<= 16384 keys each), so that one tiled pass replaces four.
 uint32_t default_mode(uint64_t n, bool /*pairs*/) { return n <= (uint64_t(1) << 22) && n >= (uint64_t(1) << 16) ? RS_MODE_MSD : RS_MODE_LSD; }
-uint32_t default_tile(int R, bool pairs) { return R == 8 ? (pairs ? 1u : 4u) : (pairs ? 1u : 4u); }
+uint32_t default_tile(int R, bool pairs) { return R == 8 ? (pairs ? 1u : 3u) : (pairs ? 1u : 4u); }
 
 // n + one tile must fit the 30-bit count field of 32-bit status words.
 bool needs_wide_status(uint64_t n) { return n + 65536 > uint64_t(StatusCodec<uint32_t>::kVal); }

@@ -82,22 +82,39 @@ __device__ __forceinline__ uint32_t find_segment(const uint32_t* tile_prefix, ui
 }
 
 // -------------------------------------------------------------- histograms
+// Each block takes a contiguous run of large tiles, so that consecutive
+// tiles usually belong to the same segment: its shared-memory histograms are
+// flushed to the segment's global arrays only when the segment changes.
 __global__ void __launch_bounds__(512) seg_hist_kernel(const SegHistArgs a) {
   __shared__ uint32_t sh[kMaxDigits * 256];
   __shared__ uint32_t s_seg[3];
   const uint32_t num_large = a.counts[SEG_NUM_LARGE], total = a.counts[SEG_NUM_TILES];
   const int nd = a.num_digits;
-  for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
-    for (int i = threadIdx.x; i < nd * 256; i += 512) sh[i] = 0u;
+  const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
+  const uint32_t t_begin = blockIdx.x * per;
+  const uint32_t t_end = t_begin + per < total ? t_begin + per : total;
+  for (int i = threadIdx.x; i < nd * 256; i += 512) sh[i] = 0u;
+  uint32_t cur = 0xffffffffu;  // large segment whose counts sit in sh
+  for (uint32_t t = t_begin; t < t_end; ++t) {
     if (threadIdx.x == 0) {
       const uint32_t li = find_segment(a.tile_prefix, num_large, t);
-      const uint32_t s = a.large_seg[li];
       s_seg[0] = li;
       s_seg[1] = t - a.tile_prefix[li];
-      s_seg[2] = s;
+      s_seg[2] = a.large_seg[li];
     }
     __syncthreads();
     const uint32_t li = s_seg[0];
+    if (li != cur) {
+      if (cur != 0xffffffffu) {
+        uint32_t* h = a.seg_hist + size_t(cur) * nd * 256;
+        for (int i = threadIdx.x; i < nd * 256; i += 512) {
+          if (sh[i]) atomicAdd(&h[i], sh[i]);
+          sh[i] = 0u;
+        }
+      }
+      cur = li;
+      __syncthreads();
+    }
     const uint64_t seg_start = a.seg_off[s_seg[2]], seg_end = a.seg_off[s_seg[2] + 1];
     const uint64_t start = seg_start + uint64_t(s_seg[1]) * a.tile;
     const uint64_t end = start + a.tile < seg_end ? start + a.tile : seg_end;
@@ -110,10 +127,11 @@ __global__ void __launch_bounds__(512) seg_hist_kernel(const SegHistArgs a) {
     // this tile's chained-scan status row starts out "not ready"
     for (int i = threadIdx.x; i < 256; i += 512) a.status[size_t(t) * 256 + i] = 0u;
     __syncthreads();
-    uint32_t* h = a.seg_hist + size_t(li) * nd * 256;
+  }
+  if (cur != 0xffffffffu) {
+    uint32_t* h = a.seg_hist + size_t(cur) * nd * 256;
     for (int i = threadIdx.x; i < nd * 256; i += 512)
       if (sh[i]) atomicAdd(&h[i], sh[i]);
-    __syncthreads();
   }
 }
 

@@ -1,0 +1,288 @@
+"""A sort-serving loop with continuous batching.
+
+Requests (uint32 keys, optionally uint32 payloads) arrive over time.  At
+each scheduler tick, the requests that have arrived are admitted while a slot
+is free and the device-memory budget allows; each admitted group becomes one
+batch: its requests are copied (pinned host -> device) into one arena, sorted
+by a single ``rs_sort_u32_segmented`` call (each request is one segment), and
+copied back (device -> pinned host), all on one of ``streams`` CUDA streams,
+so batches formed at different ticks overlap on the device.  A request's
+latency is the time from its arrival to the moment its result is back on the
+host (the batch's completion event).  Buffers stay resident: arenas and temp
+are reused from a pool keyed by size class.
+
+PyTorch is used for device memory, pinned host memory, streams and events
+only; all sorting runs in librsort's kernels.  Each request's result does not
+depend on what it was batched with (the segmented sort treats every segment
+on its own), which ``tests/test_gpu_serve.py`` checks bit for bit.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from collections import deque
+
+import numpy as np
+
+from . import rs_sort_u32, rs_sort_u32_pairs, rs_sort_u32_segmented
+
+__all__ = ["Request", "SortServer", "serial_plain", "latency_stats"]
+
+
+@dataclasses.dataclass
+class Request:
+    """One sort request.  keys / vals are pinned host tensors (int32 storage
+    of uint32 values) owned by the client; the server copies them to the
+    device and the sorted result back into out_keys / out_vals (pinned,
+    allocated with the request), with no host-side copy in between."""
+    id: int
+    arrival_s: float           # offset from the start of the run
+    keys: object               # pinned torch.int32 [n]
+    vals: object = None        # pinned torch.int32 [n] or None
+    out_keys: object = None
+    out_vals: object = None
+    done_s: float | None = None
+    batch: int | None = None
+
+    @staticmethod
+    def make(rid: int, arrival_s: float, keys: np.ndarray, vals: np.ndarray | None = None) -> "Request":
+        import torch
+        k = torch.from_numpy(np.ascontiguousarray(keys).view(np.int32)).pin_memory()
+        v = None if vals is None else torch.from_numpy(np.ascontiguousarray(vals).view(np.int32)).pin_memory()
+        r = Request(rid, arrival_s, k, v)
+        r.out_keys = torch.empty_like(k).pin_memory()
+        r.out_vals = None if v is None else torch.empty_like(v).pin_memory()
+        return r
+
+    @property
+    def n(self) -> int:
+        return int(self.keys.numel())
+
+    @property
+    def pairs(self) -> bool:
+        return self.vals is not None
+
+    def bytes_needed(self) -> int:
+        return self.n * 4 * (4 if self.pairs else 2)
+
+    def result(self):
+        """(keys, vals or None) as numpy uint32 arrays."""
+        k = self.out_keys.numpy().view(np.uint32)
+        return k, (None if self.out_vals is None else self.out_vals.numpy().view(np.uint32))
+
+
+def _size_class(nbytes: int) -> int:
+    return 1 << max(20, math.ceil(math.log2(max(nbytes, 1))))
+
+
+class _Pool:
+    """Device buffers reused by size class (powers of two, >= 1 MiB)."""
+
+    def __init__(self, device):
+        self.device = device
+        self.free: dict[int, list] = {}
+        self.bytes_held = 0
+
+    def take(self, nbytes: int):
+        import torch
+        c = _size_class(nbytes)
+        lst = self.free.get(c)
+        if lst:
+            return lst.pop()
+        self.bytes_held += c
+        return torch.empty(c, dtype=torch.uint8, device=self.device)
+
+    def give(self, buf):
+        self.free.setdefault(buf.numel(), []).append(buf)
+
+
+class _Batch:
+    def __init__(self, bid, reqs, pairs, stream, arena, temp, h_in, h_out, done_event, start_event):
+        self.id, self.reqs, self.pairs, self.stream = bid, reqs, pairs, stream
+        self.arena, self.temp, self.h_in, self.h_out = arena, temp, h_in, h_out
+        self.done_event, self.start_event = done_event, start_event
+
+
+class SortServer:
+    """Continuous-batching sort server on one GPU.
+
+    slots: batches in flight at most; streams: CUDA streams used round
+    robin; mem_budget: bytes of device memory the server may hold for
+    in-flight batches (inputs, outputs and temp); max_batch_keys: largest
+    batch arena in keys."""
+
+    def __init__(self, slots: int = 4, streams: int = 4, mem_budget: int = 8 << 30,
+                 max_batch_keys: int = 1 << 24, num_parts: int = 64, device: str = "cuda"):
+        import torch
+        self.device = torch.device(device)
+        self.slots, self.mem_budget, self.max_batch_keys = slots, mem_budget, max_batch_keys
+        self.num_parts = num_parts
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        self.pool = _Pool(self.device)
+        self.pinned = {}
+        self.in_flight: list[_Batch] = []
+        self.mem_in_use = 0
+        self.next_batch = 0
+        self.t0_event = None
+        self.t0_host = None
+
+    # -- pinned staging buffers, reused by size class
+    def _pinned(self, key, nbytes):
+        import torch
+        c = _size_class(nbytes)
+        lst = self.pinned.setdefault((key, c), [])
+        if lst:
+            return lst.pop()
+        return torch.empty(c, dtype=torch.uint8).pin_memory()
+
+    def _return_pinned(self, key, buf):
+        self.pinned.setdefault((key, buf.numel()), []).append(buf)
+
+    def _batch_bytes(self, reqs, pairs):
+        n = sum(r.n for r in reqs)
+        offs = np.zeros(len(reqs) + 1, dtype=np.uint64)
+        offs[1:] = np.cumsum([r.n for r in reqs])
+        temp = rs_sort_u32_segmented(None, 1 if pairs else None, None, 1 if pairs else None, None, offs,
+                                     len(reqs), n, self.num_parts)
+        return n * 4 * (4 if pairs else 2) + len(reqs) * 8 + temp, offs, temp
+
+    def _launch(self, reqs, pairs):
+        import torch
+        need, offs, temp_bytes = self._batch_bytes(reqs, pairs)
+        n = int(offs[-1])
+        stream = self.streams[self.next_batch % len(self.streams)]
+        words = n * (2 if pairs else 1)
+        arena = self.pool.take(2 * words * 4 + (len(reqs) + 1) * 8)
+        temp = self.pool.take(max(temp_bytes, 1))
+        h_off = self._pinned("off", (len(reqs) + 1) * 8)
+        h_off[: (len(reqs) + 1) * 8].view(torch.int64).numpy()[:] = offs.view(np.int64)
+        done = torch.cuda.Event()
+        with torch.cuda.stream(stream):
+            d_in = arena[: words * 4].view(torch.int32)
+            d_out = arena[words * 4: 2 * words * 4].view(torch.int32)
+            d_off = arena[2 * words * 4: 2 * words * 4 + (len(reqs) + 1) * 8].view(torch.int64)
+            d_off.copy_(h_off[: (len(reqs) + 1) * 8].view(torch.int64), non_blocking=True)
+            for i, r in enumerate(reqs):
+                a, e = int(offs[i]), int(offs[i + 1])
+                d_in[a:e].copy_(r.keys, non_blocking=True)
+                if pairs:
+                    d_in[n + a: n + e].copy_(r.vals, non_blocking=True)
+            kin, kout = d_in[:n], d_out[:n]
+            vin = d_in[n:] if pairs else None
+            vout = d_out[n:] if pairs else None
+            rs_sort_u32_segmented(kin, vin, kout, vout, d_off, offs, len(reqs), n, self.num_parts, None,
+                                  None, temp, stream)
+            for i, r in enumerate(reqs):
+                a, e = int(offs[i]), int(offs[i + 1])
+                r.out_keys.copy_(d_out[a:e], non_blocking=True)
+                if pairs:
+                    r.out_vals.copy_(d_out[n + a: n + e], non_blocking=True)
+            done.record(stream)
+        b = _Batch(self.next_batch, reqs, pairs, stream, arena, temp, h_off, None, done, None)
+        for r in reqs:
+            r.batch = b.id
+        self.next_batch += 1
+        self.mem_in_use += need
+        b.need = need
+        b.offs = offs
+        self.in_flight.append(b)
+
+    def _retire(self, b, now_s):
+        for r in b.reqs:
+            r.done_s = now_s
+        self.pool.give(b.arena)
+        self.pool.give(b.temp)
+        self._return_pinned("off", b.h_in)
+        self.mem_in_use -= b.need
+
+    def _poll(self):
+        now = time.perf_counter() - self.t0_host
+        still = []
+        for b in self.in_flight:
+            if b.done_event.query():
+                self._retire(b, now)
+            else:
+                still.append(b)
+        self.in_flight = still
+
+    def run(self, requests: list[Request], realtime: bool = True) -> list[Request]:
+        """Serves `requests` (sorted by arrival).  With realtime=False every
+        request counts as arrived at the start (closed-loop throughput)."""
+        import torch
+        if not realtime:  # closed loop: every request is submitted at the start
+            for r in requests:
+                r.arrival_s = 0.0
+        pending = deque(sorted(requests, key=lambda r: r.arrival_s))
+        torch.cuda.synchronize(self.device)
+        self.t0_host = time.perf_counter()
+        while pending or self.in_flight:
+            self._poll()
+            now = time.perf_counter() - self.t0_host
+            # gather arrived requests into at most two batches (keys / pairs)
+            while pending and len(self.in_flight) < self.slots:
+                if realtime and pending[0].arrival_s > now:
+                    break
+                group = {False: [], True: []}
+                budget = self.mem_budget - self.mem_in_use
+                keys_in_batch = {False: 0, True: 0}
+                while pending and (not realtime or pending[0].arrival_s <= now):
+                    r = pending[0]
+                    if keys_in_batch[r.pairs] + r.n > self.max_batch_keys and group[r.pairs]:
+                        break
+                    cost = 3 * r.bytes_needed()
+                    if cost > budget and (group[False] or group[True] or self.in_flight):
+                        break
+                    group[r.pairs].append(pending.popleft())
+                    keys_in_batch[r.pairs] += r.n
+                    budget -= cost
+                if not group[False] and not group[True]:
+                    break
+                for pairs in (False, True):
+                    if group[pairs]:
+                        self._launch(group[pairs], pairs)
+            if not self.in_flight and pending and realtime:
+                wait = pending[0].arrival_s - (time.perf_counter() - self.t0_host)
+                if wait > 0:
+                    time.sleep(min(wait, 0.002))
+            elif self.in_flight:
+                time.sleep(0.0001)
+        for s in self.streams:
+            s.synchronize()
+        return requests
+
+
+def serial_plain(requests: list[Request], num_parts: int = 64, device: str = "cuda") -> float:
+    """One request at a time on one stream: its pinned keys (and values) to
+    the device, one plain rs_sort_u32(_pairs) call, the result back into its
+    pinned output, then wait.  Returns the elapsed seconds."""
+    import torch
+    dev = torch.device(device)
+    big = max(r.n for r in requests)
+    d_k = torch.empty(big, dtype=torch.int32, device=dev)
+    d_v = torch.empty(big, dtype=torch.int32, device=dev)
+    o_k = torch.empty_like(d_k)
+    o_v = torch.empty_like(d_k)
+    temp = torch.empty(max(rs_sort_u32_pairs(None, None, None, None, big), rs_sort_u32(None, None, big)),
+                       dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for r in requests:
+        n = r.n
+        d_k[:n].copy_(r.keys, non_blocking=True)
+        if r.pairs:
+            d_v[:n].copy_(r.vals, non_blocking=True)
+            rs_sort_u32_pairs(d_k, d_v, o_k, o_v, n, num_parts, None, temp, stream)
+            r.out_vals.copy_(o_v[:n], non_blocking=True)
+        else:
+            rs_sort_u32(d_k, o_k, n, num_parts, None, temp, stream)
+        r.out_keys.copy_(o_k[:n], non_blocking=True)
+        stream.synchronize()
+    return time.perf_counter() - t0
+
+
+def latency_stats(requests: list[Request]) -> dict:
+    lat = np.array([r.done_s - r.arrival_s for r in requests])
+    return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "mean_ms": float(lat.mean() * 1e3)}

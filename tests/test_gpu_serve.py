@@ -1,0 +1,62 @@
+"""The continuous-batching server: each request's result is the same alone
+and in the mix (tolerance 0: bit for bit), and equals the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(count, seed, rate, lo=1 << 10, hi=1 << 18):
+    from paper_cs_0004013_gb300.serve import Request
+    out = []
+    for q in synth.serving_requests(count, seed, rate_per_s=rate, lo=lo, hi=hi):
+        keys = synth.uniform31(q["n"], q["seed"])
+        vals = np.arange(q["n"], dtype=np.uint32) if q["pairs"] else None
+        out.append(Request.make(q["id"], q["arrival_s"], keys, vals))
+    return out
+
+
+@pytest.mark.parametrize("realtime", [True, False])
+def test_results_identical_alone_and_in_the_mix(realtime):
+    import torch
+    import paper_cs_0004013_gb300 as rs
+    from paper_cs_0004013_gb300.serve import SortServer, latency_stats
+    reqs = _requests(60, 11, rate=2000.0)
+    srv = SortServer(slots=3, streams=3, mem_budget=1 << 30)
+    srv.run(reqs, realtime=realtime)
+    rs.rs_check_device_error()
+    assert len({r.batch for r in reqs}) > 1  # several batches were formed
+    for r in reqs:
+        got_k, got_v = r.result()
+        keys = r.keys.numpy().view(np.uint32)
+        dk = r.keys.cuda()
+        if r.pairs:
+            ko, vo, _ = rs.sort_pairs(dk, r.vals.cuda())  # the same request alone
+            torch.cuda.synchronize()
+            assert np.array_equal(got_k, ko.cpu().numpy().view(np.uint32)), r.id
+            assert np.array_equal(got_v, vo.cpu().numpy().view(np.uint32)), r.id
+            wk, wv = oracle.sort_pairs(keys, r.vals.numpy().view(np.uint32))
+            assert np.array_equal(got_v, wv)
+        else:
+            ko, _ = rs.sort(dk)
+            torch.cuda.synchronize()
+            assert np.array_equal(got_k, ko.cpu().numpy().view(np.uint32)), r.id
+            wk = oracle.sort_keys(keys)
+        assert np.array_equal(got_k, wk)
+    st = latency_stats(reqs)
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+
+
+def test_memory_budget_limits_batches():
+    """A budget smaller than two requests forces one batch at a time."""
+    import paper_cs_0004013_gb300 as rs
+    from paper_cs_0004013_gb300.serve import SortServer
+    reqs = _requests(12, 12, rate=1e6, lo=1 << 16, hi=1 << 17)
+    srv = SortServer(slots=4, streams=2, mem_budget=4 << 20)
+    srv.run(reqs, realtime=False)
+    rs.rs_check_device_error()
+    for r in reqs:
+        assert np.array_equal(r.result()[0], oracle.sort_keys(r.keys.numpy().view(np.uint32)))
