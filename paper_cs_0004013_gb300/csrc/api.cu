@@ -270,7 +270,7 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
   ha.zero_vec4 = L.status_bytes / 16;
   const HistKernel* hk = hist_kernel(p.R);
   const size_t work = (size_t(n) + 4095) / 4096;  // one block per 4096 keys at least
-  unsigned hgrid = unsigned(ds->num_sms) * 2;
+  unsigned hgrid = unsigned(ds->num_sms) * (hk->threads >= 1024 ? 1 : 2);
   if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
   RS_CUDA(traced(T_HIST, n, s, [&] { return hk->launch(ha, hgrid, s); }), "launch upfront_hist");
 
@@ -512,7 +512,7 @@ rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in
   ha.zero_ptr = reinterpret_cast<uint4*>(temp + M.base.status);
   ha.zero_vec4 = M.base.status_bytes / 16;
   const size_t work = (size_t(n) + 4095) / 4096;
-  unsigned hgrid = unsigned(ds->num_sms) * 2;
+  unsigned hgrid = unsigned(ds->num_sms);
   if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
   RS_CUDA(traced(T_HIST, n, s, [&] { return hist_kernel(8)->launch(ha, hgrid, s); }), "launch upfront_hist");
   ScanArgs sa{hist + size_t(top) * 256, bases + size_t(top) * 256, nullptr, n};
@@ -721,7 +721,7 @@ rs_status rs_digit_histograms(const uint32_t* keys, uint64_t n, uint32_t digit_b
   RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(d_hist, 0, bytes, s); }), "cudaMemsetAsync(hist)");
   if (n > 0) {
     const size_t work = (size_t(n) + 4095) / 4096;
-    unsigned grid = unsigned(ds->num_sms) * 2;
+    unsigned grid = unsigned(ds->num_sms) * (hist_kernel(int(digit_bits))->threads >= 1024 ? 1 : 2);
     if (work < grid) grid = unsigned(work);
     RS_CUDA(traced(T_HIST, double(n), s, [&] { return hist_kernel(int(digit_bits))->launch(ha, grid, s); }),
             "launch upfront_hist");

@@ -79,6 +79,71 @@ __global__ void __launch_bounds__(THREADS) upfront_hist_kernel(const HistArgs a)
   }
 }
 
+// 8-bit digits: every lane of the block counts into its own copy of the
+// histograms, laid out [digit][bin][lane] so that lane l only ever touches
+// shared-memory bank l.  No atomic ever conflicts with another (not even when
+// every key has the same digit), so the kernel runs at the speed of its
+// loads.  Copies of one warp-lane position are shared by the block's warps
+// (atomics still needed), 128 KiB of shared memory for four digits.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) upfront_hist_lanes_kernel(const HistArgs a) {
+  constexpr int BINS = 256;
+  extern __shared__ __align__(16) uint32_t sh[];  // [num_digits][256][32]
+  const int nd = a.num_digits;
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < nd * BINS * 32; i += THREADS) sh[i] = 0u;
+  __syncthreads();
+  uint32_t sft[kMaxDigits], wid[kMaxDigits];
+#pragma unroll
+  for (int j = 0; j < kMaxDigits; ++j) {
+    sft[j] = a.dig[j].shift;
+    wid[j] = a.dig[j].width;
+  }
+  auto count = [&](uint32_t k) {
+#pragma unroll
+    for (int j = 0; j < kMaxDigits; ++j)
+      if (j < nd) atomicAdd(&sh[(j * BINS + digit_of(k, sft[j], wid[j])) * 32 + lane], 1u);
+  };
+  const uint32_t n = a.n;
+  const uint32_t mis = uint32_t((reinterpret_cast<uintptr_t>(a.keys) >> 2) & 3u);
+  uint32_t head = (4u - mis) & 3u;
+  if (head > n) head = n;
+  const size_t nvec = size_t(n - head) / 4;
+  const uint32_t tail = head + uint32_t(nvec * 4);
+  if (blockIdx.x == gridDim.x - 1) {
+    for (uint32_t i = tid; i < head; i += THREADS) count(a.keys[i]);
+    for (uint32_t i = tail + tid; i < n; i += THREADS) count(a.keys[i]);
+  }
+  const uint4* v4 = reinterpret_cast<const uint4*>(a.keys + head);
+  const size_t stride = size_t(gridDim.x) * THREADS;
+  size_t i = size_t(blockIdx.x) * THREADS + tid;
+  for (; i + 3 * stride < nvec; i += 4 * stride) {
+    const uint4 x0 = ld_stream4(v4 + i);
+    const uint4 x1 = ld_stream4(v4 + i + stride);
+    const uint4 x2 = ld_stream4(v4 + i + 2 * stride);
+    const uint4 x3 = ld_stream4(v4 + i + 3 * stride);
+    count(x0.x); count(x0.y); count(x0.z); count(x0.w);
+    count(x1.x); count(x1.y); count(x1.z); count(x1.w);
+    count(x2.x); count(x2.y); count(x2.z); count(x2.w);
+    count(x3.x); count(x3.y); count(x3.z); count(x3.w);
+  }
+  for (; i < nvec; i += stride) {
+    const uint4 x = ld_stream4(v4 + i);
+    count(x.x); count(x.y); count(x.z); count(x.w);
+  }
+  for (size_t z = size_t(blockIdx.x) * THREADS + tid; z < a.zero_vec4; z += stride)
+    a.zero_ptr[z] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  // one row of 32 lane copies per (digit, bin); each thread starts its row at
+  // its own lane so that a warp's reads spread over all banks
+  for (int b = tid; b < nd * BINS; b += THREADS) {
+    uint32_t s = 0;
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) s += sh[b * 32 + ((k + lane) & 31)];
+    if (s) atomicAdd(&a.hist[b], s);
+  }
+}
+
 // One block per digit: exclusive scan of its histogram, and whether a single
 // bucket holds every key.
 template <int R>
@@ -122,12 +187,19 @@ static cudaError_t launch_scan(const ScanArgs& a, unsigned grid, cudaStream_t s)
   return cudaGetLastError();
 }
 
+template <int THREADS>
+static cudaError_t launch_hist_lanes(const HistArgs& a, unsigned grid, cudaStream_t s) {
+  const size_t smem = size_t(a.num_digits) * 256 * 32 * 4;
+  upfront_hist_lanes_kernel<THREADS><<<grid, THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 // Shared memory: 11-bit digits, 3 digits, 2 copies = 48 KiB; 8-bit digits,
-// 4 digits, 4 copies = 16 KiB.
+// 4 digits x 256 bins x 32 lane copies = 128 KiB (one block per SM).
 static const HistKernel kHist11 = {11, 512, size_t(2) * 3 * 2048 * 4, &launch_hist<11, 512, 2>,
                                    reinterpret_cast<const void*>(&upfront_hist_kernel<11, 512, 2>)};
-static const HistKernel kHist8 = {8, 512, size_t(4) * 4 * 256 * 4, &launch_hist<8, 512, 4>,
-                                  reinterpret_cast<const void*>(&upfront_hist_kernel<8, 512, 4>)};
+static const HistKernel kHist8 = {8, 1024, size_t(4) * 256 * 32 * 4, &launch_hist_lanes<1024>,
+                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024>)};
 static const ScanKernel kScan11 = {11, 1024, &launch_scan<11>};
 static const ScanKernel kScan8 = {8, 256, &launch_scan<8>};
 
