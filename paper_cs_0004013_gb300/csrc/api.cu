@@ -242,6 +242,17 @@ Layout make_layout(const SortPlan& p, uint64_t n, bool pairs) {
   return L;
 }
 
+// Blocks of a pass launch: one per tile, or for persistent kernels as many
+// as stay resident (capped by the tile count).
+unsigned pass_grid(const SortPlan& p, const DeviceState* ds) {
+  size_t g = p.num_tiles;
+  if (p.k->persistent_per_sm > 0) {
+    const size_t cap = size_t(ds->num_sms) * size_t(p.k->persistent_per_sm);
+    if (cap < g) g = cap;
+  }
+  return unsigned(g > 0 ? g : 1);
+}
+
 void part_offsets_host(uint64_t n, uint32_t parts, uint64_t* out) {
   const uint64_t q = n / parts, r = n % parts;
   for (uint64_t p = 0; p <= parts; ++p) out[p] = p * q + (p < r ? p : r);
@@ -296,7 +307,7 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
     pa.status = temp + L.status;
     pa.tile_counter = ctrl + j;
     pa.err = ds->err;
-    RS_CUDA(traced(p.R == 8 ? T_PASS8 : T_PASS11, n, s, [&] { return p.k->launch(pa, unsigned(p.num_tiles), s); }),
+    RS_CUDA(traced(p.R == 8 ? T_PASS8 : T_PASS11, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }),
             "launch onesweep");
   }
   return RS_OK;
@@ -534,7 +545,7 @@ rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in
   pa.status = temp + M.base.status;
   pa.tile_counter = ctrl;
   pa.err = ds->err;
-  RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, unsigned(p.num_tiles), s); }), "launch onesweep (top)");
+  RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }), "launch onesweep (top)");
   RS_CUDA(launch_bases_to_offsets(bases + size_t(top) * 256, 256, n, seg_off, s), "launch bucket offsets");
   return run_segmented(M.seg, temp, bk, bv, keys_out, vals_out, seg_off, 256, p.nd - 1, ds, s);
 }

@@ -1,5 +1,6 @@
 // Onesweep pass kernels with 8-bit digits (four passes over 32-bit keys).
 #include "onesweep.cuh"
+#include "onesweep_pipe.cuh"
 
 namespace rs {
 
@@ -15,6 +16,12 @@ static const OnesweepKernel kR8[] = {
     make_onesweep<8, 512, 24, false, S32, 2, false>(2), make_onesweep<8, 512, 24, true, S32, 2, false>(2),
     make_onesweep<8, 1024, 16, false, S32, 1, false>(3), make_onesweep<8, 1024, 16, true, S32, 1, false>(3),
     make_onesweep<8, 384, 20, false, S32, 2, false>(4), make_onesweep<8, 384, 20, true, S32, 2, false>(4),
+    // persistent, software-pipelined (onesweep_pipe.cuh)
+    make_onesweep_pipe<8, 512, 16, false, S32, 2>(5),   make_onesweep_pipe<8, 512, 16, true, S32, 1>(5),
+    make_onesweep_pipe<8, 256, 24, false, S32, 3>(6),   make_onesweep_pipe<8, 256, 24, true, S32, 2>(6),
+    make_onesweep_pipe<8, 384, 20, false, S32, 2>(7),   make_onesweep_pipe<8, 384, 20, true, S32, 1>(7),
+    make_onesweep_pipe<8, 512, 24, false, S32, 1>(8),   make_onesweep_pipe<8, 512, 24, true, S32, 1>(8),
+    make_onesweep_pipe<8, 256, 16, false, S32, 4>(9),   make_onesweep_pipe<8, 256, 16, true, S32, 2>(9),
 };
 
 const OnesweepKernel* onesweep_kernels_r8(int* count) {

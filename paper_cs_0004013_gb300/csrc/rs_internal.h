@@ -62,6 +62,7 @@ struct OnesweepKernel {
   size_t smem;       // dynamic shared memory bytes
   cudaError_t (*launch)(const PassArgs&, unsigned grid, cudaStream_t);
   const void* func;  // kernel symbol (for attributes)
+  int persistent_per_sm = 0;  // > 0: persistent kernel, grid = SMs x this (capped by tiles)
 };
 
 struct HistKernel {

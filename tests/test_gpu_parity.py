@@ -127,12 +127,20 @@ def test_sort_edge_values(rs, kind):
         _pairs_check(rs, keys, plan={"digit_bits": bits})
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("tile", list(range(1, 11)))
 @pytest.mark.parametrize("bits", [8, 11])
 def test_tile_shapes(rs, tile, bits):
-    keys = synth.few_distinct(5 * TILE + 999, 9)
-    _sort_check(rs, keys, plan={"digit_bits": bits, "tile": tile})
-    _pairs_check(rs, keys, plan={"digit_bits": bits, "tile": tile})
+    """Every registered tile shape (plain and persistent pipelined kernels),
+    keys and pairs, LSD mode, on sizes spanning many tiles and a ragged tail."""
+    plan = {"digit_bits": bits, "tile": tile, "mode": rs.RS_MODE_LSD}
+    try:
+        rs.temp_bytes(1000, pairs=False, plan=plan)
+    except rs.RsError:
+        pytest.skip(f"no tile shape {tile} for {bits}-bit digits")
+    for n in (5 * TILE + 999, 1 << 20, 37):
+        keys = synth.few_distinct(n, 9 + n) if n > 100 else synth.uniform31(n, 1)
+        _sort_check(rs, keys, plan=plan)
+        _pairs_check(rs, keys, plan=plan)
 
 
 @pytest.mark.parametrize("dist", sorted(synth.DISTRIBUTIONS))
