@@ -191,6 +191,14 @@ rs_status rs_trace_enable(int on);
  * kernel kind seen) and resets the trace.  *count = entries written.       */
 rs_status rs_trace_read(rs_trace_entry* out, uint32_t capacity, uint32_t* count);
 
+/* Self-test of failure detection: runs the pass kernels' cross-tile wait
+ * (the lookback) against a status row that nothing ever publishes, in
+ * temp (DEVICE, >= 4096 bytes, 256-byte aligned; cleared here).  The wait
+ * gives up after its bounded number of rounds (tens of milliseconds), raises
+ * the device error word and returns, so the next rs_check_device_error()
+ * reports RS_ERR_TIMEOUT and the context stays usable.                     */
+rs_status rs_selftest_wait_timeout(void* temp, size_t temp_bytes, rs_stream_t stream);
+
 /* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
 uint32_t rs_version(void);
 

@@ -23,7 +23,7 @@ __all__ = [
     "RsError", "RsPlan", "lib", "LIBRARY_PATH",
     "rs_sort_u32", "rs_sort_u32_pairs", "rs_sort_u32_segmented", "rs_digit_histograms",
     "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_version", "rs_trace_enable",
-    "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS",
+    "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS", "rs_selftest_wait_timeout",
     "sort", "sort_pairs", "sort_segmented", "temp_bytes", "part_offsets",
     "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD",
 ]
@@ -68,6 +68,7 @@ _SIGS = {
     "rs_version": [],
     "rs_trace_enable": [ctypes.c_int],
     "rs_sort_u32_noalloc": [_P, _P, _U64, _U32, _U64P, _P],
+    "rs_selftest_wait_timeout": [_P, ctypes.c_size_t, _P],
     "rs_trace_read": [ctypes.POINTER(RsTraceEntry), _U32, ctypes.POINTER(ctypes.c_uint32)],
 }
 
@@ -200,6 +201,11 @@ def rs_sort_u32_noalloc(keys_in, keys_out, n: int, num_parts: int = 64, stream=N
 
 def rs_check_device_error(stream=None) -> None:
     _check(lib.rs_check_device_error(_stream(stream)))
+
+
+def rs_selftest_wait_timeout(temp, stream=None) -> None:
+    """Runs the bounded-wait self-test (see include/rsort.h)."""
+    _check(lib.rs_selftest_wait_timeout(_ptr(temp), temp.numel() * temp.element_size(), _stream(stream)))
 
 
 def rs_trace_enable(on: bool = True) -> None:

@@ -847,6 +847,19 @@ rs_status rs_trace_read(rs_trace_entry* out, uint32_t capacity, uint32_t* count)
   return st;
 }
 
+rs_status rs_selftest_wait_timeout(void* temp, size_t temp_bytes, rs_stream_t stream) {
+  g_last_error.clear();
+  if (!temp || temp_bytes < 4096) return fail(RS_ERR_INVALID, "the self-test needs 4096 bytes of temp");
+  if (reinterpret_cast<uintptr_t>(temp) % kAlign) return fail(RS_ERR_INVALID, "temp is not 256-byte aligned");
+  DeviceState* ds = nullptr;
+  rs_status st = device_state(&ds);
+  if (st != RS_OK) return st;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  RS_CUDA(cudaMemsetAsync(temp, 0, 4096, s), "cudaMemsetAsync(self-test)");
+  RS_CUDA(launch_lookback_timeout(static_cast<const uint32_t*>(temp), ds->err, s), "launch self-test");
+  return RS_OK;
+}
+
 uint32_t rs_version(void) { return kVersion; }
 
 }  // extern "C"

@@ -167,6 +167,9 @@ cudaError_t launch_local_sort(const LocalArgs& a, bool small, bool pairs, unsign
 cudaError_t launch_bases_to_offsets(const uint32_t* bases, uint32_t num, uint64_t n, uint64_t* seg_off,
                                     cudaStream_t s);
 
+// Self-test of the bounded lookback wait (selftest.cu).
+cudaError_t launch_lookback_timeout(const uint32_t* status, uint32_t* err, cudaStream_t s);
+
 // Sets the calling thread's message for rs_last_error() (printf format).
 void set_last_error(int status, const char* fmt, ...);
 
