@@ -22,6 +22,10 @@ static const OnesweepKernel kR8[] = {
     make_onesweep_pipe<8, 384, 20, false, S32, 2>(7),   make_onesweep_pipe<8, 384, 20, true, S32, 1>(7),
     make_onesweep_pipe<8, 512, 24, false, S32, 1>(8),   make_onesweep_pipe<8, 512, 24, true, S32, 1>(8),
     make_onesweep_pipe<8, 256, 16, false, S32, 4>(9),   make_onesweep_pipe<8, 256, 16, true, S32, 2>(9),
+    // smaller blocks, more of them per SM
+    make_onesweep<8, 256, 24, false, S32, 4, false>(10), make_onesweep<8, 256, 24, true, S32, 3, false>(10),
+    make_onesweep<8, 256, 32, false, S32, 3, false>(11), make_onesweep<8, 256, 32, true, S32, 2, false>(11),
+    make_onesweep<8, 384, 24, false, S32, 2, false>(12), make_onesweep<8, 384, 24, true, S32, 2, false>(12),
 };
 
 const OnesweepKernel* onesweep_kernels_r8(int* count) {
