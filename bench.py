@@ -170,6 +170,23 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------- replicas
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time (the job's time) when ranks run replicas."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(keys_per_rank: int, world: int, steps: int, job_ms: float) -> float:
+    """Gkeys/s of the whole job: every rank's keys over the slowest time."""
+    return world * keys_per_rank * steps / (job_ms * 1e-3) / 1e9
+
+
 # ------------------------------------------------------------------ ours
 def traffic_from_profiles(kernel_file: str, key: str):
     """DRAM bytes per launch recorded by ncu for the pass kernel, valid only
@@ -245,13 +262,9 @@ def run_ours(args):
     rs.rs_trace_enable(False)
     rs.rs_check_device_error()
     trace = rs.rs_trace_read()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_per_step = ms / args.steps
-    value = world * n * args.steps / (ms * 1e-3) / 1e9
+    value = whole_job_rate(n, world, args.steps, ms)
 
     # bytes of the executed plan: one read for the histograms, then a read
     # and a write per pass (keys; plus payload for pairs)
@@ -296,12 +309,8 @@ def run_ours(args):
             e2e_step()
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ems], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * n * args.steps / (ems * 1e-3) / 1e9, "unit": "Gkeys/s",
+        ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": whole_job_rate(n, world, args.steps, ems), "unit": "Gkeys/s",
                "h2d_bytes_per_step": 4 * n, "d2h_bytes_per_step": 4 * n}
         ok = np.array_equal(h_out.numpy().view(np.uint32)[:: max(1, n // 4096)],
                             np.sort(keys)[:: max(1, n // 4096)])
