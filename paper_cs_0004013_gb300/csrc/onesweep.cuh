@@ -42,6 +42,15 @@
 
 namespace rs {
 
+// Width of the per-warp lane-mask table: 2^kMaskBits slots indexed by the
+// digit's low kMaskBits bits; wider digits tell their remaining bits apart
+// with one ballot per bit.  (A 32-slot table, one slot per shared-memory
+// bank, avoids the table's bank conflicts but its three extra ballots per
+// 8-bit key cost more issue slots than the conflicts: measured 312 vs 283 us
+// per 2^26-key pass on GB300.)
+constexpr int kMaskBits = 8;
+constexpr uint32_t kMaskSlots = 1u << kMaskBits;
+
 // DPT consecutive 16-bit counters, two per 32-bit word.  Sums of two halves
 // never carry into each other because every count is at most TILE < 2^16.
 template <int DPT>
@@ -101,7 +110,7 @@ struct OnesweepLayout {
   static constexpr int DPT = DIGITS / DTH;
   // per-warp lane-mask table on the digit's low 8 bits, then per-warp
   // 16-bit running counters per digit
-  static constexpr size_t MASK_BYTES = size_t(WARPS) * 256 * 4;
+  static constexpr size_t MASK_BYTES = size_t(WARPS) * kMaskSlots * 4;
   static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;
   static constexpr size_t RANK_BYTES = MASK_BYTES + CNT_BYTES;
   static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
@@ -241,12 +250,13 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, uint32_t fi
 // Stable rank of ITEMS keys per thread within their warp (item j of lane l
 // is the warp's key j*32 + l).  Lanes holding the same digit find each other
 // through the warp's table of lane masks (shared-memory atomicOr, then a
-// read-back); digits wider than 8 bits index the table by their low 8 bits
-// and split the rest off with one ballot per bit.  The highest lane of a
+// read-back) indexed by the digit's low kMaskBits bits; the other bits are
+// split off with one ballot per bit.  The highest lane of a
 // group advances the warp's running count for the digit and clears the
 // table slot.  A warp whose 32 digits are all equal skips the table.  Ranks
-// are < 2^16, two per register.  wm / wc: this warp's mask table (256
-// words, zero) and counters (2^R halfwords, zero on the first call).
+// are < 2^16, two per register.  wm / wc: this warp's mask table
+// (kMaskSlots words, zero) and counters (2^R halfwords, zero on the first
+// call).
 template <int R, int ITEMS>
 __device__ __forceinline__ void warp_rank(const uint32_t (&key)[ITEMS], uint32_t shift, uint32_t width, uint32_t* wm,
                                           uint16_t* wc, uint32_t (&rk)[(ITEMS + 1) / 2]) {
@@ -263,10 +273,10 @@ __device__ __forceinline__ void warp_rank(const uint32_t (&key)[ITEMS], uint32_t
       __syncwarp();
       r = before + lane;
     } else {
-      const uint32_t lo = d & 255u;
+      const uint32_t lo = d & (kMaskSlots - 1u);
       uint32_t same_hi = 0xffffffffu;
 #pragma unroll
-      for (int b = 8; b < R; ++b) {
+      for (int b = kMaskBits; b < R; ++b) {
         const uint32_t bit = (d >> b) & 1u;
         const uint32_t bl = __ballot_sync(0xffffffffu, bit);
         same_hi &= bit ? bl : ~bl;
@@ -307,7 +317,7 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
   constexpr int DIGITS = L::DIGITS, WARPS = L::WARPS, TILE = L::TILE;
   constexpr int DTH = L::DTH, DPT = L::DPT;
-  // rank tables ([WARPS][256] lane masks, then [WARPS][DIGITS] 16-bit
+  // rank tables ([WARPS][kMaskSlots] lane masks, then [WARPS][DIGITS] 16-bit
   // counters), aliased by the staging buffer once positions are final
   uint32_t* s_mask = reinterpret_cast<uint32_t*>(smem);
   uint16_t* s_cnt = reinterpret_cast<uint16_t*>(smem + L::MASK_BYTES);
@@ -337,7 +347,7 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
 
   // 2. rank within the warp
   uint32_t rk[(ITEMS + 1) / 2];
-  warp_rank<R, ITEMS>(key, shift, width, s_mask + warp * 256, s_cnt + warp * DIGITS, rk);
+  warp_rank<R, ITEMS>(key, shift, width, s_mask + warp * kMaskSlots, s_cnt + warp * DIGITS, rk);
   __syncthreads();
 
   // 3. per-digit tile counts -> aggregate status; counts -> exclusive

@@ -28,7 +28,7 @@ struct PipeLayout {
   static constexpr int DIGITS = 1 << R;
   static constexpr int WARPS = THREADS / 32;
   static constexpr int TILE = THREADS * ITEMS;
-  static constexpr size_t MASK_BYTES = size_t(WARPS) * 256 * 4;
+  static constexpr size_t MASK_BYTES = size_t(WARPS) * kMaskSlots * 4;
   static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;
   static constexpr size_t RANK_BYTES = (MASK_BYTES + CNT_BYTES + 15) / 16 * 16;
   static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_pipe_kernel(const Pass
     const uint32_t valid = left < size_t(TILE) ? uint32_t(left) : uint32_t(TILE);
     // rank within the warp
     uint32_t rk[(ITEMS + 1) / 2];
-    warp_rank<R, ITEMS>(key, shift, width, s_mask + warp * 256, s_cnt + warp * DIGITS, rk);
+    warp_rank<R, ITEMS>(key, shift, width, s_mask + warp * kMaskSlots, s_cnt + warp * DIGITS, rk);
     __syncthreads();
     // per digit: tile count -> aggregate status; exclusive (digit, warp) prefixes
     uint32_t tot = 0, loff = 0;

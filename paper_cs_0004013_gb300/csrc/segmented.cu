@@ -179,7 +179,7 @@ template <int THREADS, int ITEMS, bool PAIRS>
 struct LocalLayout {
   static constexpr int WARPS = THREADS / 32;
   static constexpr int TILE = THREADS * ITEMS;
-  static constexpr size_t MASK_BYTES = size_t(WARPS) * 256 * 4;
+  static constexpr size_t MASK_BYTES = size_t(WARPS) * kMaskSlots * 4;
   static constexpr size_t CNT_BYTES = size_t(WARPS) * 256 * 2;
   static constexpr size_t OFF_BUF = MASK_BYTES + CNT_BYTES;
   static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(THREADS, 1) local_sort_kernel(const LocalArgs 
       for (int i = tid; i < int(L::OFF_BUF / 16); i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
       __syncthreads();
       uint32_t rk[(ITEMS + 1) / 2];
-      warp_rank<8, ITEMS>(key, shift, width, s_mask + warp * 256, s_cnt + warp * 256, rk);
+      warp_rank<8, ITEMS>(key, shift, width, s_mask + warp * kMaskSlots, s_cnt + warp * 256, rk);
       __syncthreads();
       // per digit (threads 0..255): total over warps, exclusive over digits,
       // then exclusive (digit, warp) offsets
