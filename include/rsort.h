@@ -132,6 +132,31 @@ rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in,
                         uint32_t shift, uint32_t width, void* temp,
                         size_t* temp_bytes, rs_stream_t stream);
 
+/* ---- host buffers ------------------------------------------------------- */
+
+/* rs_sort_u32 / rs_sort_u32_pairs on HOST arrays: the keys (and values) are
+ * copied into device buffers carved from temp, sorted there, and copied back
+ * into h_keys_out (and h_vals_out), all enqueued on `stream` in that order.
+ * No counterpart in the paper (its keys were already in the cells' memory).
+ *   h_keys_in, h_keys_out: HOST, n uint32 each; h_vals_in, h_vals_out: HOST,
+ *     n uint32 each, or both NULL for a keys-only sort.  The host outputs
+ *     must not overlap the host inputs.
+ *   temp: DEVICE; its size (query with temp == NULL) is that of the device
+ *     sort plus 2 (keys only) or 4 (pairs) buffers of n uint32.
+ * Page-locked host memory (cudaHostAlloc, cudaHostRegister) makes the
+ * copies asynchronous; with pageable memory they still run in stream order,
+ * but the CUDA runtime may block the caller during them.  The host outputs
+ * are complete once the stream has passed the call's work (synchronise it or
+ * wait on an event recorded after the call).  Calls on different streams,
+ * each with its own temp, overlap on the GPU: one call's device-to-host copy
+ * runs while the next one copies in and sorts, which keeps the host link
+ * busy in both directions when a stream of host arrays is sorted.          */
+rs_status rs_sort_u32_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
+                           uint32_t* h_keys_out, uint32_t* h_vals_out, uint64_t n,
+                           uint32_t num_parts, uint64_t* h_part_offsets,
+                           const rs_plan* plan, void* temp, size_t* temp_bytes,
+                           rs_stream_t stream);
+
 /* ---- sorting without any device allocation ------------------------------ */
 
 /* Largest n accepted by rs_sort_u32_noalloc. */

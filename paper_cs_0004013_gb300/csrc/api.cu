@@ -86,11 +86,12 @@ rs_status device_state(DeviceState** out) {
 // ---- tracing -------------------------------------------------------------------
 enum TraceKind {
   T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_SEGPLAN, T_SEGHIST, T_SEGSCAN, T_SEGPASS, T_LOCAL,
-  T_KINDS
+  T_H2D, T_D2H, T_KINDS
 };
 const char* const kTraceNames[T_KINDS] = {"clear",       "upfront_hist", "digit_scan", "onesweep_r8",
                                           "onesweep_r11", "seg_part_offsets", "seg_plan", "seg_hist",
-                                          "seg_scan",    "seg_pass",     "local_sort"};
+                                          "seg_scan",    "seg_pass",     "local_sort", "copy_h2d",
+                                          "copy_d2h"};
 struct TraceRec {
   int kind;
   double keys;
@@ -643,6 +644,68 @@ rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in, ui
                             const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
   return sort_impl(keys_in, vals_in, keys_out, vals_out, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
                    reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+rs_status rs_sort_u32_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in, uint32_t* h_keys_out,
+                           uint32_t* h_vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
+                           const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
+  g_last_error.clear();
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool pairs = h_vals_in != nullptr;
+  if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
+  if (!pairs && h_vals_out) return fail(RS_ERR_INVALID, "h_vals_out given without h_vals_in");
+  if (pairs && !h_vals_out) return fail(RS_ERR_INVALID, "h_vals_in given without h_vals_out");
+  if (n >= (uint64_t(1) << 32)) return fail(RS_ERR_INVALID, "n = %llu: must be below 2^32", (unsigned long long)n);
+  // device copies of the arrays first, then the device sort's own scratch
+  const size_t nb = size_t(n) * 4, slot = align_up(nb);
+  const int nbuf = pairs ? 4 : 2;
+  size_t sort_bytes = 0;
+  rs_status st = sort_impl(nullptr, nullptr, nullptr, nullptr, n, num_parts, nullptr, plan, nullptr, &sort_bytes, s,
+                           pairs);
+  if (st != RS_OK) return st;
+  const size_t need = nbuf * slot + sort_bytes;
+  if (!temp) {
+    *temp_bytes = need;
+    return RS_OK;
+  }
+  if (reinterpret_cast<uintptr_t>(temp) % kAlign) return fail(RS_ERR_INVALID, "temp is not 256-byte aligned");
+  if (*temp_bytes < need) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, need);
+  if (n > 0) {
+    if (!h_keys_in || !h_keys_out) return fail(RS_ERR_INVALID, "NULL host key buffer");
+    const void* ins[2] = {h_keys_in, h_vals_in};
+    const void* outs[2] = {h_keys_out, h_vals_out};
+    for (const void* o : outs)
+      for (const void* i : ins)
+        if (overlaps(o, nb, i, nb)) return fail(RS_ERR_INVALID, "a host output overlaps a host input");
+    if (pairs && overlaps(h_keys_out, nb, h_vals_out, nb)) return fail(RS_ERR_INVALID, "h_keys_out and h_vals_out overlap");
+  }
+  unsigned char* t = static_cast<unsigned char*>(temp);
+  uint32_t* d_kin = reinterpret_cast<uint32_t*>(t);
+  uint32_t* d_kout = reinterpret_cast<uint32_t*>(t + slot);
+  uint32_t* d_vin = pairs ? reinterpret_cast<uint32_t*>(t + 2 * slot) : nullptr;
+  uint32_t* d_vout = pairs ? reinterpret_cast<uint32_t*>(t + 3 * slot) : nullptr;
+  if (n == 0) {  // num_parts was checked by the size query above
+    if (h_part_offsets) part_offsets_host(0, num_parts, h_part_offsets);
+    return RS_OK;
+  }
+  RS_CUDA(traced(T_H2D, double(n), s,
+                 [&] { return cudaMemcpyAsync(d_kin, h_keys_in, nb, cudaMemcpyHostToDevice, s); }),
+          "cudaMemcpyAsync(keys to device)");
+  if (pairs)
+    RS_CUDA(traced(T_H2D, double(n), s,
+                   [&] { return cudaMemcpyAsync(d_vin, h_vals_in, nb, cudaMemcpyHostToDevice, s); }),
+            "cudaMemcpyAsync(values to device)");
+  size_t sb = sort_bytes;
+  st = sort_impl(d_kin, d_vin, d_kout, d_vout, n, num_parts, h_part_offsets, plan, t + nbuf * slot, &sb, s, pairs);
+  if (st != RS_OK) return st;
+  RS_CUDA(traced(T_D2H, double(n), s,
+                 [&] { return cudaMemcpyAsync(h_keys_out, d_kout, nb, cudaMemcpyDeviceToHost, s); }),
+          "cudaMemcpyAsync(keys to host)");
+  if (pairs)
+    RS_CUDA(traced(T_D2H, double(n), s,
+                   [&] { return cudaMemcpyAsync(h_vals_out, d_vout, nb, cudaMemcpyDeviceToHost, s); }),
+            "cudaMemcpyAsync(values to host)");
+  return RS_OK;
 }
 
 rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out,

@@ -104,3 +104,36 @@ def test_partition_offsets_host_path_needs_no_gpu():
     st = r.lib.rs_sort_u32(None, None, 0, 64, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), None,
                            ctypes.c_void_p(1 << 28), ctypes.byref(sz), None)
     assert st == 0 and not offs.any()
+
+
+def test_host_entry_sizes_and_checks():
+    """rs_sort_u32_host: its temp is the device sort's plus device copies of
+    the arrays; argument errors are caught before any copy."""
+    import numpy as np
+    import paper_cs_0004013_gb300 as r
+    n = 1000
+    slot = (4 * n + 255) // 256 * 256
+    assert r.rs_sort_u32_host(None, None, None, None, n) == r.rs_sort_u32(None, None, n) + 2 * slot
+    assert (r.rs_sort_u32_host(None, 1, None, 2, n)
+            == r.rs_sort_u32_pairs(None, None, None, None, n) + 4 * slot)
+    for args in ((None, 1, None, None), (None, None, None, 2)):  # values on one side only
+        with pytest.raises(r.RsError):
+            r.rs_sort_u32_host(*args, n)
+    with pytest.raises(r.RsError):
+        r.rs_sort_u32_host(None, None, None, None, n, num_parts=0)
+    need = r.rs_sort_u32_host(None, None, None, None, n)
+    keys = np.zeros(2 * n, dtype=np.uint32)
+    base = keys.ctypes.data
+    sz = ctypes.c_size_t(need)
+    st = r.lib.rs_sort_u32_host(base, None, base + 400, None, n, 64, None, None, ctypes.c_void_p(1 << 28),
+                                ctypes.byref(sz), None)
+    assert st == 1 and "overlap" in r.rs_last_error()
+    sz = ctypes.c_size_t(need - 1)
+    st = r.lib.rs_sort_u32_host(base, None, base + 4 * n, None, n, 64, None, None, ctypes.c_void_p(1 << 28),
+                                ctypes.byref(sz), None)
+    assert st == 2
+    offs = np.ones(65, dtype=np.uint64)
+    sz = ctypes.c_size_t(r.rs_sort_u32_host(None, None, None, None, 0))
+    st = r.lib.rs_sort_u32_host(None, None, None, None, 0, 64, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                None, ctypes.c_void_p(1 << 28), ctypes.byref(sz), None)
+    assert st == 0 and not offs.any()
