@@ -167,16 +167,19 @@ rs_status pick_kernel(int R, uint32_t tile_idx, bool pairs, bool wide, const One
   int cnt = 0;
   const OnesweepKernel* ks = R == 8 ? onesweep_kernels_r8(&cnt) : onesweep_kernels_r11(&cnt);
   const int shape = tile_idx == 0 ? 0 : int(tile_idx) - 1;
-  bool any = false;
+  bool any = false, any_payload = false;
   for (int i = 0; i < cnt; ++i) {
     if (ks[i].shape != shape) continue;
     any = true;
+    any_payload |= ks[i].pairs == pairs;
     if (ks[i].pairs == pairs && ks[i].wide_status == wide) {
       *out = &ks[i];
       return RS_OK;
     }
   }
   if (!any) return fail(RS_ERR_UNSUPPORTED, "tile shape %u not available for %d-bit digits", tile_idx, R);
+  if (!any_payload)
+    return fail(RS_ERR_UNSUPPORTED, "tile shape %u has no %s kernel", tile_idx, pairs ? "key+value" : "keys-only");
   return fail(RS_ERR_UNSUPPORTED, "tile shape %u has no %s-status kernel (n too large for it)", tile_idx,
               wide ? "64-bit" : "32-bit");
 }

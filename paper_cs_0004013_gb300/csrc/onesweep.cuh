@@ -398,8 +398,12 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   auto do_lookback = [&]() {
     if (tid < DTH) {
       uint32_t prefix[DPT];
-      // fewer loads in flight when keys and ranks are still live
-      constexpr int LBW = EARLY_LB ? ((8 / DPT) > 1 ? 8 / DPT : 1) : ((32 / DPT) > 1 ? 32 / DPT : 1);
+      // About eight status words per thread and round: the nearest
+      // inclusive predecessor is usually a few tiles back, and wider windows
+      // cost more issue slots than the rounds they save (GB300, 2^26 keys:
+      // 271 vs 282 us per 512 x 24 pass with 8 vs 32 words, 390 vs 434 us
+      // per 11-bit pass with 4 vs 16 rows of two digits).
+      constexpr int LBW = (8 / DPT) > 1 ? 8 / DPT : 1;
       lookback<DIGITS, DPT, S, LBW>(status, tile, job.first, d0, parity, err, prefix);
       if (tile != job.first) {
         S* mine = status + size_t(tile) * DIGITS + d0;

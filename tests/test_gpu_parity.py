@@ -137,10 +137,16 @@ def test_tile_shapes(rs, tile, bits):
         rs.temp_bytes(1000, pairs=False, plan=plan)
     except rs.RsError:
         pytest.skip(f"no tile shape {tile} for {bits}-bit digits")
+    try:
+        rs.temp_bytes(1000, pairs=True, plan=plan)
+        with_pairs = True
+    except rs.RsError:  # a keys-only shape
+        with_pairs = False
     for n in (5 * TILE + 999, 1 << 20, 37):
         keys = synth.few_distinct(n, 9 + n) if n > 100 else synth.uniform31(n, 1)
         _sort_check(rs, keys, plan=plan)
-        _pairs_check(rs, keys, plan=plan)
+        if with_pairs:
+            _pairs_check(rs, keys, plan=plan)
 
 
 @pytest.mark.parametrize("dist", sorted(synth.DISTRIBUTIONS))
