@@ -6,7 +6,11 @@ is free and the device-memory budget allows; each admitted group becomes one
 batch: its requests are copied (pinned host -> device) into one arena, sorted
 by a single ``rs_sort_u32_segmented`` call (each request is one segment), and
 copied back (device -> pinned host), all on one of ``streams`` CUDA streams,
-so batches formed at different ticks overlap on the device.  A request's
+so batches formed at different ticks overlap on the device.  A request of at
+least ``direct_min_keys`` keys forms a batch of its own, sorted by one
+``rs_sort_u32_host`` call straight from and into its pinned buffers (the
+plain sort's kernels, no arena); one such batch's copy back then overlaps the
+next one's copy in and sort.  A request's
 latency is the time from its arrival to the moment its result is back on the
 host (the batch's completion event).  Buffers stay resident: arenas and temp
 are reused from a pool keyed by size class.
@@ -25,7 +29,7 @@ from collections import deque
 
 import numpy as np
 
-from . import rs_sort_u32, rs_sort_u32_pairs, rs_sort_u32_segmented
+from . import rs_sort_u32, rs_sort_u32_host, rs_sort_u32_pairs, rs_sort_u32_segmented
 
 __all__ = ["Request", "SortServer", "serial_plain", "latency_stats"]
 
@@ -110,13 +114,16 @@ class SortServer:
     slots: batches in flight at most; streams: CUDA streams used round
     robin; mem_budget: bytes of device memory the server may hold for
     in-flight batches (inputs, outputs and temp); max_batch_keys: largest
-    batch arena in keys."""
+    batch arena in keys; direct_min_keys: requests this large are sorted on
+    their own, from and into their pinned buffers."""
 
     def __init__(self, slots: int = 4, streams: int = 4, mem_budget: int = 8 << 30,
-                 max_batch_keys: int = 1 << 24, num_parts: int = 64, device: str = "cuda"):
+                 max_batch_keys: int = 1 << 24, num_parts: int = 64, device: str = "cuda",
+                 direct_min_keys: int = 1 << 22):
         import torch
         self.device = torch.device(device)
         self.slots, self.mem_budget, self.max_batch_keys = slots, mem_budget, max_batch_keys
+        self.direct_min_keys = direct_min_keys
         self.num_parts = num_parts
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
         self.pool = _Pool(self.device)
@@ -147,8 +154,26 @@ class SortServer:
                                      len(reqs), n, self.num_parts)
         return n * 4 * (4 if pairs else 2) + len(reqs) * 8 + temp, offs, temp
 
+    def _launch_direct(self, r):
+        import torch
+        stream = self.streams[self.next_batch % len(self.streams)]
+        need = rs_sort_u32_host(None, r.vals, None, r.out_vals, r.n, self.num_parts)
+        temp = self.pool.take(need)
+        done = torch.cuda.Event()
+        rs_sort_u32_host(r.keys, r.vals, r.out_keys, r.out_vals, r.n, self.num_parts, None, temp, stream,
+                         want_offsets=False)
+        done.record(stream)
+        b = _Batch(self.next_batch, [r], r.pairs, stream, None, temp, None, None, done, None)
+        r.batch = b.id
+        self.next_batch += 1
+        self.mem_in_use += need
+        b.need = need
+        self.in_flight.append(b)
+
     def _launch(self, reqs, pairs):
         import torch
+        if len(reqs) == 1 and reqs[0].n >= self.direct_min_keys:
+            return self._launch_direct(reqs[0])
         need, offs, temp_bytes = self._batch_bytes(reqs, pairs)
         n = int(offs[-1])
         stream = self.streams[self.next_batch % len(self.streams)]
@@ -191,9 +216,10 @@ class SortServer:
     def _retire(self, b, now_s):
         for r in b.reqs:
             r.done_s = now_s
-        self.pool.give(b.arena)
+        if b.arena is not None:
+            self.pool.give(b.arena)
+            self._return_pinned("off", b.h_in)
         self.pool.give(b.temp)
-        self._return_pinned("off", b.h_in)
         self.mem_in_use -= b.need
 
     def _poll(self):
@@ -230,12 +256,16 @@ class SortServer:
                     r = pending[0]
                     if keys_in_batch[r.pairs] + r.n > self.max_batch_keys and group[r.pairs]:
                         break
+                    if r.n >= self.direct_min_keys and (group[False] or group[True]):
+                        break  # sorted on its own, at the next admission
                     cost = 3 * r.bytes_needed()
                     if cost > budget and (group[False] or group[True] or self.in_flight):
                         break
                     group[r.pairs].append(pending.popleft())
                     keys_in_batch[r.pairs] += r.n
                     budget -= cost
+                    if r.n >= self.direct_min_keys:
+                        break
                 if not group[False] and not group[True]:
                     break
                 for pairs in (False, True):

@@ -60,3 +60,33 @@ def test_memory_budget_limits_batches():
     rs.rs_check_device_error()
     for r in reqs:
         assert np.array_equal(r.result()[0], oracle.sort_keys(r.keys.numpy().view(np.uint32)))
+
+
+@pytest.mark.parametrize("realtime", [True, False])
+def test_direct_and_batched_requests_mixed(realtime):
+    """Requests at or above direct_min_keys are sorted on their own through
+    the host-buffer entry point, the rest in segmented batches: every result
+    equals the oracle's, whichever way it went."""
+    import paper_cs_0004013_gb300 as rs
+    from paper_cs_0004013_gb300.serve import SortServer
+    reqs = _requests(40, 13, rate=5000.0, lo=1 << 12, hi=1 << 19)
+    srv = SortServer(slots=4, streams=3, mem_budget=1 << 30, direct_min_keys=1 << 16)
+    srv.run(reqs, realtime=realtime)
+    rs.rs_check_device_error()
+    big = [r for r in reqs if r.n >= 1 << 16]
+    small = [r for r in reqs if r.n < 1 << 16]
+    assert big and small
+    batches = {}
+    for r in reqs:
+        batches.setdefault(r.batch, []).append(r)
+    for r in big:
+        assert batches[r.batch] == [r]  # alone in its batch
+    for r in reqs:
+        got_k, got_v = r.result()
+        keys = r.keys.numpy().view(np.uint32)
+        if r.pairs:
+            wk, wv = oracle.sort_pairs(keys, r.vals.numpy().view(np.uint32))
+            assert np.array_equal(got_v, wv), r.id
+        else:
+            wk = oracle.sort_keys(keys)
+        assert np.array_equal(got_k, wk), r.id
