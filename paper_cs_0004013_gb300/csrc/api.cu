@@ -71,10 +71,11 @@ rs_status device_state(DeviceState** out) {
               "cudaFuncSetAttribute(hist)");
     }
     const SegKernels* sk = seg_kernels();
-    const void* fn[6] = {sk->pass_keys, sk->pass_pairs, sk->tiny_keys, sk->tiny_pairs, sk->small_keys, sk->small_pairs};
-    const size_t sm[6] = {sk->pass_smem_keys,  sk->pass_smem_pairs,  sk->tiny_smem_keys,
-                          sk->tiny_smem_pairs, sk->small_smem_keys, sk->small_smem_pairs};
-    for (int i = 0; i < 6; ++i)
+    const void* fn[7] = {sk->pass_keys,  sk->pass_pairs,  sk->tiny_keys, sk->tiny_pairs,
+                         sk->small_keys, sk->small_pairs, sk->hist};
+    const size_t sm[7] = {sk->pass_smem_keys,  sk->pass_smem_pairs,  sk->tiny_smem_keys, sk->tiny_smem_pairs,
+                          sk->small_smem_keys, sk->small_smem_pairs, sk->hist_smem};
+    for (int i = 0; i < 7; ++i)
       RS_CUDA(cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm[i])),
               "cudaFuncSetAttribute(segmented)");
     st.ready = true;
@@ -150,15 +151,18 @@ struct SortPlan {
   size_t num_tiles = 0;
 };
 
-// Defaults from measurement on GB300 at n = 2^26 (uniform 31-bit keys):
-// 8-bit digits beat 11-bit ones because the 11-bit lookback walks 2048
-// status words per tile; the 512 x 24 tile (shape 2) wins for keys, the
-// 512 x 16 tile (shape 0) for pairs (which need twice the staging memory).
+// Defaults from measurement on GB300 (uniform 31-bit keys, 2^16 .. 2^26):
+// 8-bit digits beat 11-bit ones (four 512 x 24 passes take less time than
+// three 11-bit ones); LSD beats the MSD plan at every size (the MSD plan's
+// extra launches cost more than the three tiled passes it saves); the
+// 512 x 24 tile (shape 2) wins for keys above 2^22, the 512 x 16 tile
+// (shape 0) below that and for pairs (which need twice the staging memory).
 int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 8; }
-// MSD when the 256 top-digit buckets of a uniform input fit the one-block
-// local sort (<= 16384 keys each), so that one tiled pass replaces four.
-uint32_t default_mode(uint64_t n, bool /*pairs*/) { return n <= (uint64_t(1) << 22) && n >= (uint64_t(1) << 16) ? RS_MODE_MSD : RS_MODE_LSD; }
-uint32_t default_tile(int R, bool pairs) { return R == 8 ? (pairs ? 1u : 3u) : (pairs ? 1u : 4u); }
+uint32_t default_mode(uint64_t /*n*/, bool /*pairs*/) { return RS_MODE_LSD; }
+uint32_t default_tile(int R, bool pairs, uint64_t n) {
+  if (R == 8) return (pairs || n <= (uint64_t(1) << 22)) ? 1u : 3u;
+  return pairs ? 1u : 4u;
+}
 
 // n + one tile must fit the 30-bit count field of 32-bit status words.
 bool needs_wide_status(uint64_t n) { return n + 65536 > uint64_t(StatusCodec<uint32_t>::kVal); }
@@ -200,7 +204,7 @@ rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p) {
     ++p->nd;
   }
   const bool wide = needs_wide_status(n);
-  uint32_t tile = (user && user->tile) ? user->tile : default_tile(p->R, pairs);
+  uint32_t tile = (user && user->tile) ? user->tile : default_tile(p->R, pairs, n);
   if (wide && !(user && user->tile)) tile = 1;  // only shape 0 has 64-bit status kernels
   rs_status st = pick_kernel(p->R, tile, pairs, wide, &p->k);
   if (st != RS_OK) return st;
@@ -324,7 +328,7 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
 // are sorted src -> dst in shared memory.
 struct SegLayout {
   size_t counts = 0, seg_hist = 0, seg_bases = 0, large_seg = 0, tile_prefix = 0, small_seg = 0, tiny_seg = 0;
-  size_t status = 0, alt_k = 0, alt_v = 0, end = 0;
+  size_t status = 0, jobs = 0, alt_k = 0, alt_v = 0, end = 0;
   size_t memset_from = 0, memset_bytes = 0;  // counts + seg_hist
   size_t tiles_ub = 0;
 };
@@ -352,6 +356,8 @@ SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int n
   off = align_up(off + size_t(num_segs) * 4);
   L.status = off;
   off = align_up(off + L.tiles_ub * 256 * 4);
+  L.jobs = off;
+  off = align_up(off + L.tiles_ub * sizeof(SegTileJob));
   L.alt_k = off;
   off = align_up(off + size_t(total_n) * 4);
   if (pairs) {
@@ -396,7 +402,8 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
   for (int j = 0; j < nd; ++j) ha.dig[j] = dig[j];
   ha.seg_hist = reinterpret_cast<uint32_t*>(temp + L.seg_hist);
   ha.status = reinterpret_cast<uint32_t*>(temp + L.status);
-  RS_CUDA(traced(T_SEGHIST, 0, s, [&] { return launch_seg_hist(ha, cap(L.tiles_ub, size_t(sms) * 4), s); }),
+  ha.jobs = reinterpret_cast<SegTileJob*>(temp + L.jobs);
+  RS_CUDA(traced(T_SEGHIST, 0, s, [&] { return launch_seg_hist(ha, cap(L.tiles_ub, size_t(sms)), s); }),
           "launch seg_hist");
   SegScanArgs sa{ha.seg_hist, reinterpret_cast<uint32_t*>(temp + L.seg_bases), counts, nd};
   RS_CUDA(traced(T_SEGSCAN, 0, s, [&] { return launch_seg_scan(sa, cap(num_segs, size_t(sms) * 4), s); }),
@@ -412,11 +419,9 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
     ga.kout = to_out ? kout : alt_k;
     ga.vin = src_v;
     ga.vout = pairs ? (to_out ? vout : alt_v) : nullptr;
-    ga.seg_off = seg_off;
-    ga.large_seg = pa.large_seg;
-    ga.tile_prefix = pa.tile_prefix;
     ga.counts = counts;
     ga.seg_bases = sa.seg_bases;
+    ga.jobs = ha.jobs;
     ga.num_digits = nd;
     ga.pass = p;
     ga.shift = dig[p].shift;

@@ -97,6 +97,19 @@ struct SegPlanArgs {
   uint32_t* counts;         // [kSegCountWords]
 };
 
+// Where one tile of a large segment lies (written by seg_hist, read by
+// every seg_pass launch so that a tile costs one lookup).
+struct SegTileJob {
+  uint64_t base;       // index of the tile's first key
+  uint32_t valid;      // keys in the tile
+  uint32_t first;      // first tile of the segment
+  uint32_t out_start;  // segment start and end in the output
+  uint32_t out_end;
+  uint32_t li;         // index of the segment among the large ones
+  uint32_t reserved;
+};
+static_assert(sizeof(SegTileJob) == 32, "two 16-byte words per tile");
+
 struct SegHistArgs {
   const uint32_t* keys;
   const uint64_t* seg_off;
@@ -108,6 +121,7 @@ struct SegHistArgs {
   DigitSpec dig[kMaxDigits];
   uint32_t* seg_hist;  // [num_large][num_digits][256], zeroed before the launch
   uint32_t* status;    // [tiles][256]; each tile's row is cleared here
+  SegTileJob* jobs;    // [tiles]; written here
 };
 
 struct SegScanArgs {
@@ -122,11 +136,9 @@ struct SegPassArgs {
   uint32_t* kout;
   const uint32_t* vin;
   uint32_t* vout;
-  const uint64_t* seg_off;
-  const uint32_t* large_seg;
-  const uint32_t* tile_prefix;
   const uint32_t* counts;
   const uint32_t* seg_bases;
+  const SegTileJob* jobs;
   int num_digits, pass;
   uint32_t shift, width;
   uint32_t* status;
@@ -156,6 +168,8 @@ struct SegKernels {
   const void* tiny_pairs;
   const void* small_keys;
   const void* small_pairs;
+  const void* hist;
+  size_t hist_smem;
 };
 
 const SegKernels* seg_kernels();

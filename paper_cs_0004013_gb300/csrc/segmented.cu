@@ -83,56 +83,90 @@ __device__ __forceinline__ uint32_t find_segment(const uint32_t* tile_prefix, ui
 
 // -------------------------------------------------------------- histograms
 // Each block takes a contiguous run of large tiles, so that consecutive
-// tiles usually belong to the same segment: its shared-memory histograms are
-// flushed to the segment's global arrays only when the segment changes.
-__global__ void __launch_bounds__(512) seg_hist_kernel(const SegHistArgs a) {
-  __shared__ uint32_t sh[kMaxDigits * 256];
-  __shared__ uint32_t s_seg[3];
+// tiles usually belong to the same segment.  Every lane counts into its own
+// copy of the digit histograms, laid out [digit][bin][lane] so that lane l
+// only touches shared-memory bank l (no atomic conflicts whatever the
+// digits); the copies are summed into the segment's global arrays when the
+// run moves on to the next segment, and at the end.  Also writes each
+// tile's job entry and clears its chained-scan status row.
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs a) {
+  extern __shared__ __align__(16) uint32_t sh[];  // [num_digits][256][32]
   const uint32_t num_large = a.counts[SEG_NUM_LARGE], total = a.counts[SEG_NUM_TILES];
   const int nd = a.num_digits;
+  const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t per = (total + gridDim.x - 1) / gridDim.x;
   const uint32_t t_begin = blockIdx.x * per;
   const uint32_t t_end = t_begin + per < total ? t_begin + per : total;
-  for (int i = threadIdx.x; i < nd * 256; i += 512) sh[i] = 0u;
-  uint32_t cur = 0xffffffffu;  // large segment whose counts sit in sh
-  for (uint32_t t = t_begin; t < t_end; ++t) {
-    if (threadIdx.x == 0) {
-      const uint32_t li = find_segment(a.tile_prefix, num_large, t);
-      s_seg[0] = li;
-      s_seg[1] = t - a.tile_prefix[li];
-      s_seg[2] = a.large_seg[li];
+  if (t_begin >= t_end) return;  // uniform across the block
+  for (int i = tid; i < nd * 256 * 32; i += THREADS) sh[i] = 0u;
+  uint32_t sft[kMaxDigits], wid[kMaxDigits];
+#pragma unroll
+  for (int j = 0; j < kMaxDigits; ++j) {
+    sft[j] = a.dig[j].shift;
+    wid[j] = a.dig[j].width;
+  }
+  // sums a segment's lane copies into its global histograms and zeroes them;
+  // each thread owns whole (digit, bin) rows and starts at its own lane, so
+  // that a warp's reads spread over all banks
+  auto flush = [&](uint32_t li) {
+    __syncthreads();
+    uint32_t* h = a.seg_hist + size_t(li) * nd * 256;
+    for (int r = tid; r < nd * 256; r += THREADS) {
+      uint32_t sum = 0;
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        uint32_t* c = &sh[r * 32 + ((k + lane) & 31)];
+        sum += *c;
+        *c = 0u;
+      }
+      if (sum) atomicAdd(&h[r], sum);
     }
     __syncthreads();
-    const uint32_t li = s_seg[0];
-    if (li != cur) {
-      if (cur != 0xffffffffu) {
-        uint32_t* h = a.seg_hist + size_t(cur) * nd * 256;
-        for (int i = threadIdx.x; i < nd * 256; i += 512) {
-          if (sh[i]) atomicAdd(&h[i], sh[i]);
-          sh[i] = 0u;
-        }
-      }
-      cur = li;
-      __syncthreads();
+  };
+  // the segment of the run's first tile; later ones are found by stepping
+  uint32_t li = find_segment(a.tile_prefix, num_large, t_begin);
+  uint32_t first = a.tile_prefix[li], next = a.tile_prefix[li + 1];
+  uint32_t s = a.large_seg[li];
+  uint64_t seg_start = a.seg_off[s], seg_end = a.seg_off[s + 1];
+  __syncthreads();
+  for (uint32_t t = t_begin; t < t_end; ++t) {
+    if (t >= next) {  // uniform: every thread steps the same way
+      flush(li);
+      do {
+        ++li;
+        first = next;
+        next = a.tile_prefix[li + 1];
+      } while (t >= next);
+      s = a.large_seg[li];
+      seg_start = a.seg_off[s];
+      seg_end = a.seg_off[s + 1];
     }
-    const uint64_t seg_start = a.seg_off[s_seg[2]], seg_end = a.seg_off[s_seg[2] + 1];
-    const uint64_t start = seg_start + uint64_t(s_seg[1]) * a.tile;
+    const uint64_t start = seg_start + uint64_t(t - first) * a.tile;
     const uint64_t end = start + a.tile < seg_end ? start + a.tile : seg_end;
-    for (uint64_t i = start + threadIdx.x; i < end; i += 512) {
-      const uint32_t k = ld_stream(a.keys + i);
+    if (tid == 0)
+      a.jobs[t] = SegTileJob{start, uint32_t(end - start), first, uint32_t(seg_start), uint32_t(seg_end), li, 0u};
+    // eight loads in flight per thread before the counting (measured faster
+    // than two 16-byte vectors per thread)
+    for (uint64_t i0 = start + tid; i0 < end; i0 += 8 * THREADS) {
+      uint32_t k[8];
 #pragma unroll
-      for (int j = 0; j < kMaxDigits; ++j)
-        if (j < nd) atomicAdd(&sh[j * 256 + digit_of(k, a.dig[j].shift, a.dig[j].width)], 1u);
+      for (int u = 0; u < 8; ++u) {
+        const uint64_t i = i0 + uint64_t(u) * THREADS;
+        k[u] = i < end ? ld_stream(a.keys + i) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (i0 + uint64_t(u) * THREADS >= end) break;
+#pragma unroll
+        for (int j = 0; j < kMaxDigits; ++j)
+          if (j < nd) atomicAdd(&sh[(j * 256 + digit_of(k[u], sft[j], wid[j])) * 32 + lane], 1u);
+      }
     }
     // this tile's chained-scan status row starts out "not ready"
-    for (int i = threadIdx.x; i < 256; i += 512) a.status[size_t(t) * 256 + i] = 0u;
-    __syncthreads();
+    for (int i = tid; i < 256; i += THREADS) a.status[size_t(t) * 256 + i] = 0u;
   }
-  if (cur != 0xffffffffu) {
-    uint32_t* h = a.seg_hist + size_t(cur) * nd * 256;
-    for (int i = threadIdx.x; i < nd * 256; i += 512)
-      if (sh[i]) atomicAdd(&h[i], sh[i]);
-  }
+  flush(li);
 }
 
 __global__ void __launch_bounds__(256) seg_scan_kernel(const SegScanArgs a) {
@@ -152,22 +186,19 @@ template <int THREADS, int ITEMS, bool PAIRS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) seg_pass_kernel(const SegPassArgs a) {
   using L = OnesweepLayout<8, THREADS, ITEMS, PAIRS>;
   extern __shared__ __align__(16) unsigned char smem[];
-  const uint32_t num_large = a.counts[SEG_NUM_LARGE], total = a.counts[SEG_NUM_TILES];
+  const uint32_t total = a.counts[SEG_NUM_TILES];
   for (;;) {
     const uint32_t t = begin_tile<8, THREADS, ITEMS, PAIRS>(a.tile_counter, smem);
     if (t >= total) return;  // uniform across the block
-    const uint32_t li = find_segment(a.tile_prefix, num_large, t);
-    const uint32_t s = a.large_seg[li];
-    const uint64_t seg_start = a.seg_off[s], seg_end = a.seg_off[s + 1];
+    const SegTileJob jb = a.jobs[t];
     TileJob job;
     job.tile = t;
-    job.first = a.tile_prefix[li];
-    job.base = seg_start + size_t(t - job.first) * L::TILE;
-    const uint64_t left = seg_end - job.base;
-    job.valid = left < uint64_t(L::TILE) ? uint32_t(left) : uint32_t(L::TILE);
-    job.out_start = uint32_t(seg_start);
-    job.out_end = uint32_t(seg_end);
-    job.bases = a.seg_bases + (size_t(li) * a.num_digits + a.pass) * 256;
+    job.first = jb.first;
+    job.base = jb.base;
+    job.valid = jb.valid;
+    job.out_start = jb.out_start;
+    job.out_end = jb.out_end;
+    job.bases = a.seg_bases + (size_t(jb.li) * a.num_digits + a.pass) * 256;
     onesweep_tile<8, THREADS, ITEMS, PAIRS, uint32_t, false>(job, a.kin, a.kout, a.vin, a.vout, a.shift, a.width,
                                                               a.status, a.parity, a.err, smem);
     __syncthreads();  // the next tile reuses shared memory
@@ -292,6 +323,9 @@ cudaError_t launch_local(const LocalArgs& a, unsigned grid, cudaStream_t s) {
 constexpr int kSegThreads = 512, kSegItems = 16;
 // Local sorts: tiny segments <= 256 x 16 keys, small ones <= 1024 x 16 keys.
 constexpr int kTinyThreads = 256, kSmallThreads = 1024, kLocalItems = 16;
+// Segment histograms: one 1024-thread block per SM (lane copies of up to
+// four digits take 128 KiB).
+constexpr int kSegHistThreads = 1024;
 
 const SegKernels* seg_kernels() {
   static const SegKernels k = {
@@ -310,6 +344,8 @@ const SegKernels* seg_kernels() {
       reinterpret_cast<const void*>(&local_sort_kernel<kTinyThreads, kLocalItems, true>),
       reinterpret_cast<const void*>(&local_sort_kernel<kSmallThreads, kLocalItems, false>),
       reinterpret_cast<const void*>(&local_sort_kernel<kSmallThreads, kLocalItems, true>),
+      reinterpret_cast<const void*>(&seg_hist_kernel<kSegHistThreads>),
+      size_t(kMaxDigits) * 256 * 32 * 4,
   };
   return &k;
 }
@@ -319,7 +355,7 @@ cudaError_t launch_seg_plan(const SegPlanArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_seg_hist(const SegHistArgs& a, unsigned grid, cudaStream_t s) {
-  seg_hist_kernel<<<grid, 512, 0, s>>>(a);
+  seg_hist_kernel<kSegHistThreads><<<grid, kSegHistThreads, size_t(a.num_digits) * 256 * 32 * 4, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_seg_scan(const SegScanArgs& a, unsigned grid, cudaStream_t s) {

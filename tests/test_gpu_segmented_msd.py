@@ -107,3 +107,26 @@ def test_msd_skewed_top_byte(rs):
     torch.cuda.synchronize()
     rs.rs_check_device_error()
     assert np.array_equal(to_host_u32(ko), oracle.sort_keys(keys))
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_segmented_unaligned_views(rs, shift):
+    """Key and value arrays that start 4, 8 or 12 bytes past a 16-byte
+    boundary (every kernel of the pipeline reads them through unaligned
+    views)."""
+    import torch
+    sizes = [20_000, 3, 70_001, 16_385, 40_000]
+    n = int(sum(sizes))
+    keys = synth.uniform31(n, 90 + shift)
+    vals = np.arange(n, dtype=np.uint32)
+    pad = np.zeros(shift, np.uint32)
+    dk = to_dev(np.concatenate([pad, keys]))[shift:]
+    dv = to_dev(np.concatenate([pad, vals]))[shift:]
+    offs = np.zeros(len(sizes) + 1, np.uint64)
+    offs[1:] = np.cumsum(sizes)
+    ko, vo, po = rs.sort_segmented(dk, dv, offs)
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk, wv, _ = oracle.sort_segmented(keys, vals, offs, 64)
+    assert np.array_equal(to_host_u32(ko), wk)
+    assert np.array_equal(to_host_u32(vo), wv)
