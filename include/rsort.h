@@ -10,8 +10,8 @@
  *    partitions take the extra element (footnote 7 of Sec. 3.4.2), so
  *    partition p starts at  off[p] = p * floor(n / P) + min(p, n mod P).
  *  - Sec. 3.2 / 3.3.1 / 5: the sort is a radix distribution: per digit, a
- *    histogram of the digit ("increment bucket"), its cumulative totals,
- *    and a stable "partial sort" that groups keys by bucket in ascending
+ *    histogram of the digit (one count per key in its bucket), its cumulative
+ *    totals, and a stable partial sort that groups keys by bucket in ascending
  *    bucket order, repeated from the low digit to the high one with the
  *    earlier order kept.  Pairs are therefore sorted STABLY by key.
  *
@@ -123,7 +123,7 @@ rs_status rs_digit_histograms(const uint32_t* keys, uint64_t n, uint32_t digit_b
                               rs_stream_t stream);
 
 /* One stable distribution of (keys, vals) by the digit of `width` bits at
- * `shift` (the "partial sort" of Sec. 3.2; one pass of Sec. 3.3.1):
+ * `shift` (the partial sort of Sec. 3.2; one pass of Sec. 3.3.1):
  * keys grouped by digit value, in ascending order, input order kept within
  * a digit value.  vals_in/vals_out may both be NULL.  width must be 1..11
  * and shift + width <= 32.  Temp as for the sorts.                          */

@@ -25,7 +25,7 @@ its definition, so that every kernel step can be checked on its own:
 * ``digit_bases``: the cumulative bucket totals of Sec. 3.2, exclusive, i.e.
   the number of keys whose digit is smaller (Sec. 4.4 orders it as
   cumulative-then-sum, which gives the same numbers);
-* ``distribute``: one stable distribution by a digit, the "partial sort" of
+* ``distribute``: one stable distribution by a digit, the partial sort of
   Sec. 3.2 (grouped by bucket, buckets ascending) that keeps the earlier order
   (Sec. 3.3.1);
 * ``skippable_digits``: a digit on which every key agrees moves nothing; the

@@ -1,8 +1,9 @@
 // Upfront digit histograms (every digit in one read of the keys) and their
 // exclusive scans.
 //
-// Paper: the count loop of the bucketing phase ("increment bucket to which
-// element[i] belongs", Sec. 3.2) followed by the cumulative totals (Sec. 3.2;
+// Paper: the count loop of the bucketing phase, where each element adds one
+// to the counter of its bucket (Sec. 3.2), here over every digit of the keys'
+// order-preserving unsigned map, followed by the cumulative totals (Sec. 3.2;
 // Sec. 4.4 sums the per-cell totals after making them cumulative).  On the
 // AP1000 each cell counted its own elements and a hypercube summation added
 // the 64 arrays (Sec. 4.4); here each block counts a slice of the keys into
@@ -31,7 +32,9 @@ __global__ void __launch_bounds__(THREADS) upfront_hist_kernel(const HistArgs a)
     sft[j] = a.dig[j].shift;
     wid[j] = a.dig[j].width;
   }
+  const KeyXform xf = a.xform;
   auto count = [&](uint32_t k) {
+    k = to_ordered(k, xf);
 #pragma unroll
     for (int j = 0; j < kMaxDigits; ++j)
       if (j < nd) atomicAdd(&my[j * DIGITS + digit_of(k, sft[j], wid[j])], 1u);
@@ -99,7 +102,9 @@ __global__ void __launch_bounds__(THREADS, 1) upfront_hist_lanes_kernel(const Hi
     sft[j] = a.dig[j].shift;
     wid[j] = a.dig[j].width;
   }
+  const KeyXform xf = a.xform;
   auto count = [&](uint32_t k) {
+    k = to_ordered(k, xf);
 #pragma unroll
     for (int j = 0; j < kMaxDigits; ++j)
       if (j < nd) atomicAdd(&sh[(j * BINS + digit_of(k, sft[j], wid[j])) * 32 + lane], 1u);

@@ -5,7 +5,7 @@
 // tile as one contiguous run.
 //
 // Paper: the pass is the bucketing/distribution step of Sec. 3.2 (count per
-// bucket, cumulative totals, "partial sort" grouping keys by bucket in
+// bucket, cumulative totals, the partial sort grouping keys by bucket in
 // ascending order, distribution of contiguous bucket ranges), done exactly:
 // the per-cell-per-bucket offsets the paper chose not to compute (which
 // left up to 128 elements misplaced, fixed later by post-balancing) come

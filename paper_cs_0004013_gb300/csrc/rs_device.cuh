@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "rs_internal.h"
+
 namespace rs {
 
 // Rounds of the cross-tile lookback a tile waits on a predecessor that has
@@ -26,6 +28,16 @@ __device__ __forceinline__ uint32_t lanemask_gt() {
   asm("mov.u32 %0, %%lanemask_gt;" : "=r"(m));
   return m;
 }
+
+// The order-preserving map of KeyXform and its inverse (the inverse looks at
+// the mapped word's top bit, which is the complement of the key's sign).
+__device__ __forceinline__ uint32_t to_ordered(uint32_t k, KeyXform x) {
+  return k ^ ((uint32_t(int32_t(k) >> 31) & x.fmask) ^ x.smask);
+}
+__device__ __forceinline__ uint32_t from_ordered(uint32_t t, KeyXform x) {
+  return t ^ ((uint32_t(~int32_t(t) >> 31) & x.fmask) ^ x.smask);
+}
+__device__ __forceinline__ bool is_identity(KeyXform x) { return (x.fmask | x.smask) == 0u; }
 
 // Digit of `width` bits at `shift` (width >= 1, shift + width <= 32).
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t shift, uint32_t width) {

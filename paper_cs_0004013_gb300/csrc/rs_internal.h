@@ -13,6 +13,19 @@ struct DigitSpec {
   uint32_t shift, width;
 };
 
+// Order-preserving map of a 32-bit key word onto an unsigned one, so that
+// signed and IEEE-754 binary32 keys sort by the same unsigned radix passes
+// (the paper sorts positive integers, Sec. 1.1):
+//   ordered = key ^ ((sign(key) ? fmask : 0) ^ smask)
+// unsigned: (0, 0); two's-complement signed: (0, 0x80000000), the sign bit
+// flipped; binary32: (0x7fffffff, 0x80000000), every bit of a negative value
+// flipped and the sign bit of a non-negative one (the total order
+// -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN of IEEE 754 totalOrder).
+struct KeyXform {
+  uint32_t fmask, smask;
+};
+constexpr KeyXform kIdentityXform = {0u, 0u};
+
 // Upfront histogram (one read of the keys, every digit at once) and zeroing
 // of the chained-scan status array.
 struct HistArgs {
@@ -23,6 +36,7 @@ struct HistArgs {
   uint32_t* hist;      // [num_digits][2^R], zeroed before the launch
   uint4* zero_ptr;     // region to clear (status words), may be null
   size_t zero_vec4;    // its size in 16-byte units
+  KeyXform xform;      // applied to every key before its digits are taken
 };
 
 // Exclusive scan of each digit's histogram + skip flags.
@@ -49,6 +63,8 @@ struct PassArgs {
   void* status;              // [num_tiles][2^R] status words
   uint32_t* tile_counter;    // this pass's tile ticket, zeroed before the launch
   uint32_t* err;             // device error word
+  KeyXform xin;              // applied to keys read from keys_in
+  KeyXform xout;             // inverted on keys written to keys_out
 };
 
 struct OnesweepKernel {
@@ -122,6 +138,7 @@ struct SegHistArgs {
   uint32_t* seg_hist;  // [num_large][num_digits][256], zeroed before the launch
   uint32_t* status;    // [tiles][256]; each tile's row is cleared here
   SegTileJob* jobs;    // [tiles]; written here
+  KeyXform xform;      // applied to every key before its digits are taken
 };
 
 struct SegScanArgs {
@@ -145,6 +162,7 @@ struct SegPassArgs {
   uint32_t* tile_counter;
   uint32_t parity;
   uint32_t* err;
+  KeyXform xin, xout;  // applied on loading kin, inverted on storing kout
 };
 
 struct LocalArgs {
@@ -157,6 +175,7 @@ struct LocalArgs {
   const uint32_t* count;  // device count of list entries
   int num_digits;
   DigitSpec dig[kMaxDigits];
+  KeyXform xin, xout;     // applied on loading kin, inverted on storing kout
 };
 
 struct SegKernels {
