@@ -37,9 +37,17 @@ N_KEYS = 1 << 26
 WORKLOAD = "plain sort of 2^26 uint32 keys uniform in [0, 2^31-1], keys only, 64 partitions"
 
 
-def workload_label(n: int, pairs: bool) -> str:
+KEY_KINDS = {"u32": 0, "i32": 1, "f32": 2}
+
+
+def workload_label(n: int, pairs: bool, key_kind: str = "u32") -> str:
     size = f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)
     w = WORKLOAD.replace("2^26", size)
+    if key_kind == "i32":
+        w = w.replace("uint32 keys uniform in [0, 2^31-1]", "int32 keys uniform over all 2^32 values")
+    elif key_kind == "f32":
+        w = w.replace("uint32 keys uniform in [0, 2^31-1]",
+                      "float32 keys (uniform 32-bit patterns, IEEE totalOrder)")
     return w.replace("keys only", "key+payload") if pairs else w
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 126 * 1024 * 1024
@@ -57,6 +65,8 @@ def parse():
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--pairs", action="store_true", help="time key+payload sorts as the main value")
+    ap.add_argument("--key-kind", choices=["u32", "i32", "f32"], default="u32",
+                    help="how the 32-bit key words are ordered (u32: the headline workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", choices=["plain", "batched", "serve", "dist"], default="plain",
@@ -135,23 +145,43 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ cpu baseline
-def cpu_baseline(sample_keys: int = 1 << 22, budget_s: float = 12.0):
+def workload_keys(n: int, seed: int, key_kind: str) -> np.ndarray:
+    """The timed workload's keys: uniform 31-bit keys (the headline), or
+    for signed / binary32 kinds every 32-bit pattern (both signs; NaNs,
+    infinities and denormals for binary32)."""
+    import synth
+    if key_kind == "u32":
+        return synth.uniform31(n, seed)
+    return synth.splitmix64(seed, (n + 1) // 2).view(np.uint32)[:n].copy()
+
+
+def sorted_by_kind(keys: np.ndarray, key_kind: str) -> np.ndarray:
+    """Sanity reference for the end-to-end check (not the oracle): the words
+    in order of their kind through the order-preserving unsigned map."""
+    f, m = {"u32": (0, 0), "i32": (0, 0x80000000), "f32": (0x7FFFFFFF, 0x80000000)}[key_kind]
+    sign = (keys >> np.uint32(31)).astype(bool)
+    t = np.sort(keys ^ (np.where(sign, np.uint32(f), np.uint32(0)) ^ np.uint32(m)))
+    top = (t >> np.uint32(31)).astype(bool)  # the complement of the original sign
+    return t ^ (np.where(top, np.uint32(0), np.uint32(f)) ^ np.uint32(m))
+
+
+def cpu_baseline(sample_keys: int = 1 << 22, budget_s: float = 12.0, key_kind: str = "u32"):
     """The oracle as it stands (numpy stable sort, one core) on a bounded
-    sample of the workload: repeated sorts of 2^22 uniform keys."""
+    sample of the workload: repeated sorts of 2^22 of its keys."""
     import oracle
     import synth
-    keys = synth.uniform31(sample_keys, synth.CONFIG_SEED + 2)
+    keys = workload_keys(sample_keys, synth.CONFIG_SEED + 2, key_kind)
     t0 = time.perf_counter()
     reps = 0
     while True:
-        oracle.sort_keys(keys)
+        oracle.sort_keys(keys, key_kind)
         reps += 1
         el = time.perf_counter() - t0
         if el > budget_s or reps >= 50:
             break
     rate = reps * sample_keys / el / 1e9
     return {"value": rate, "unit": "Gkeys/s", "cores": 1, "kind": "oracle",
-            "sample": f"{reps} sorts of 2^22 uniform 31-bit keys (numpy stable sort), {el:.1f} s"}
+            "sample": f"{reps} sorts of 2^22 of the workload's keys ({key_kind}; numpy stable sort), {el:.1f} s"}
 
 
 def run_reference(args):
@@ -230,10 +260,10 @@ def run_ours(args):
 
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
-    keys = synth.uniform31(n, synth.CONFIG_SEED + 2 + 1000 * rank)
+    keys = workload_keys(n, synth.CONFIG_SEED + 2 + 1000 * rank, args.key_kind)
     d_keys = torch.from_numpy(keys.view(np.int32)).to(dev)
     d_out = torch.empty_like(d_keys)
-    plan = {"digit_bits": args.digit_bits, "tile": args.tile}
+    plan = {"digit_bits": args.digit_bits, "tile": args.tile, "key_kind": KEY_KINDS[args.key_kind]}
     pairs = args.pairs
     if pairs:
         d_vals = torch.arange(n, dtype=torch.int32, device=dev)
@@ -373,20 +403,20 @@ def run_ours(args):
                "api": "rs_sort_u32_host (pinned host buffers; copies of consecutive sorts overlap)"}
         for tmp, h_out, h_vout in slots:
             ok = np.array_equal(h_out.numpy().view(np.uint32)[:: max(1, n // 4096)],
-                                np.sort(keys)[:: max(1, n // 4096)])
+                                sorted_by_kind(keys, args.key_kind)[:: max(1, n // 4096)])
             if not ok:
                 raise SystemExit("end-to-end output is not the sorted keys")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(key_kind=args.key_kind)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": workload_label(n, pairs),
+            "config": {"workload": workload_label(n, pairs, args.key_kind),
                        "n": n, "digit_bits": args.digit_bits or "auto", "passes": passes,
                        "algorithmic_bytes_per_key": bpk,
                        "sort_roofline_frac": value / world * 1e9 * bpk / (peak * 1e9),

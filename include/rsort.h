@@ -54,8 +54,8 @@ typedef enum rs_status {
   RS_ERR_UNSUPPORTED = 5     /* a plan field this build does not offer */
 } rs_status;
 
-/* Radix plan.  Zero fields mean "choose automatically" (the autotuner's
- * table, keyed by n and the payload flag).
+/* Radix plan.  Zero fields mean "choose automatically" (the library's
+ * defaults, measured per size class) or, for key_kind, unsigned keys.
  *   digit_bits: 8 (four passes over 32-bit keys) or 11 (three passes,
  *               11 + 11 + 10 bits).  The paper's bucketing used 12-13 bit
  *               buckets (Sec. 3.2, Sec. 4.7) and planned a 16 + 15-bit
@@ -64,13 +64,25 @@ typedef enum rs_status {
  *               RS_MODE_MSD = bucket by the top digit first, then sort each
  *               bucket locally (the bucketing + local sort pipeline of
  *               Sec. 3 / Sec. 4.6).
- *   tile:       1 + index of the kernel tile shape (0 = automatic).         */
+ *   tile:       1 + index of the kernel tile shape (0 = automatic).
+ *   key_kind:   how the 32-bit key words are ordered.  RS_KEY_U32: unsigned
+ *               (the paper's integers, Sec. 1.1); RS_KEY_I32: two's-complement
+ *               signed; RS_KEY_F32: IEEE-754 binary32 in the totalOrder of
+ *               IEEE 754-2008 Sec. 5.10 (-NaN < -inf < ... < -0 < +0 < ... <
+ *               +inf < +NaN, NaNs by payload).  Every entry point that takes
+ *               a plan honours it; the output holds the input's words, only
+ *               their order depends on the kind.  The passes run on an
+ *               order-preserving unsigned map of each word (sign bit flipped;
+ *               for negative binary32 values every bit) taken when a key is
+ *               read from the input and undone when it is written to the
+ *               output, so the work and traffic are those of unsigned keys. */
 enum { RS_MODE_AUTO = 0, RS_MODE_LSD = 1, RS_MODE_MSD = 2 };
+enum { RS_KEY_U32 = 0, RS_KEY_I32 = 1, RS_KEY_F32 = 2 };
 typedef struct rs_plan {
   uint32_t digit_bits;
   uint32_t mode;
   uint32_t tile;
-  uint32_t reserved;
+  uint32_t key_kind;
 } rs_plan;
 
 /* Sort n keys ascending into keys_out and write the num_parts + 1 partition

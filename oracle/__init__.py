@@ -11,8 +11,11 @@ definition written out with numpy, with no blocking, fusion or reordering:
 * the sorted output is the keys in ascending unsigned order (Sec. 1.1: cell 0
   holds the lowest values, cell 63 the highest);
 * with a payload, equal keys keep their input order: the method is a radix
-  sort whose low-order "sort" is retained while the higher digits are sorted
-  (Sec. 3.3.1), and the order inside a bucket must survive distribution (Sec. 5);
+  sort in which the order reached on the lower digits survives the sorting by
+  the higher ones (Sec. 3.3.1), and the order inside a bucket must survive
+  distribution (Sec. 5);
+* key words of other kinds (``order_perm``): two's-complement signed, and
+  IEEE-754 binary32 in the standard's totalOrder (IEEE 754-2008 Sec. 5.10);
 * the output is split into ``P`` (= 64) equal contiguous partitions, the lower
   partitions taking the extra element when P does not divide n (Sec. 1.1, and
   the rule in footnote 7 of Sec. 3.4.2 that the lower cell gets the odd datum).
@@ -38,6 +41,8 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = [
+    "KINDS",
+    "order_perm",
     "sort_keys",
     "sort_pairs",
     "partition_offsets",
@@ -60,19 +65,52 @@ def _u32(a) -> np.ndarray:
     return a
 
 
-def sort_keys(keys) -> np.ndarray:
-    """Keys in ascending unsigned 32-bit order (Sec. 1.1)."""
-    return np.sort(_u32(keys), kind="stable")
+KINDS = ("u32", "i32", "f32")
 
 
-def sort_pairs(keys, vals) -> tuple[np.ndarray, np.ndarray]:
+def order_perm(keys, kind: str = "u32") -> np.ndarray:
+    """The stable permutation that puts 32-bit key words in ascending order
+    of their ``kind``:
+
+    * ``u32``: unsigned integers (Sec. 1.1);
+    * ``i32``: two's-complement signed integers;
+    * ``f32``: IEEE-754 binary32 values in the totalOrder of IEEE 754-2008
+      Sec. 5.10: a value with the sign bit set comes before one without (so
+      -NaN < -inf < -0 < +0 < +inf < +NaN); among negative ones the larger
+      magnitude (the low 31 bits read as an integer, NaN payloads included)
+      comes first, among non-negative ones the smaller.
+    """
+    w = _u32(keys)
+    if kind == "u32":
+        return np.argsort(w, kind="stable")
+    if kind == "i32":
+        return np.argsort(w.view(np.int32), kind="stable")
+    if kind == "f32":
+        negative = (w >> np.uint32(31)).astype(bool)
+        magnitude = (w & np.uint32(0x7FFFFFFF)).astype(np.int64)
+        within = np.where(negative, -magnitude, magnitude)
+        sign_class = np.where(negative, 0, 1)
+        return np.lexsort((within, sign_class))  # the last key is the primary one; lexsort is stable
+    raise ValueError(f"unknown key kind {kind!r}")
+
+
+def sort_keys(keys, kind: str = "u32") -> np.ndarray:
+    """Keys in ascending order of their kind (unsigned by default, Sec. 1.1);
+    the words themselves are returned unchanged."""
+    if kind == "u32":
+        return np.sort(_u32(keys), kind="stable")
+    w = _u32(keys)
+    return w[order_perm(w, kind)]
+
+
+def sort_pairs(keys, vals, kind: str = "u32") -> tuple[np.ndarray, np.ndarray]:
     """(key, value) pairs ordered by key alone; equal keys keep input order
     (Sec. 3.3.1, Sec. 5)."""
     keys = _u32(keys)
     vals = _u32(vals)
     if keys.shape != vals.shape:
         raise ValueError("keys and vals differ in length")
-    perm = np.argsort(keys, kind="stable")
+    perm = order_perm(keys, kind)
     return keys[perm], vals[perm]
 
 
@@ -87,7 +125,7 @@ def partition_offsets(n: int, num_parts: int = 64) -> np.ndarray:
     return p * np.uint64(q) + np.minimum(p, np.uint64(r))
 
 
-def sort_segmented(keys, vals, seg_offsets, num_parts: int = 64):
+def sort_segmented(keys, vals, seg_offsets, num_parts: int = 64, kind: str = "u32"):
     """Each segment [seg_offsets[s], seg_offsets[s+1]) sorted on its own
     (stable by key when ``vals`` is given), with the segment's partition
     offsets made absolute by adding the segment start.  Returns
@@ -101,9 +139,9 @@ def sort_segmented(keys, vals, seg_offsets, num_parts: int = 64):
     for s in range(nseg):
         a, b = int(seg_offsets[s]), int(seg_offsets[s + 1])
         if vals is None:
-            ko[a:b] = sort_keys(keys[a:b])
+            ko[a:b] = sort_keys(keys[a:b], kind)
         else:
-            ko[a:b], vo[a:b] = sort_pairs(keys[a:b], _u32(vals)[a:b])
+            ko[a:b], vo[a:b] = sort_pairs(keys[a:b], _u32(vals)[a:b], kind)
         po[s] = partition_offsets(b - a, num_parts) + np.uint64(a)
     return ko, vo, po
 

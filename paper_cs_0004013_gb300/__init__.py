@@ -26,12 +26,14 @@ __all__ = [
     "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS", "rs_selftest_wait_timeout",
     "rs_sort_u32_host",
     "sort", "sort_pairs", "sort_segmented", "temp_bytes", "part_offsets",
-    "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD",
+    "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD", "RS_KEY_U32", "RS_KEY_I32", "RS_KEY_F32",
 ]
 
 STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_TEMP_TOO_SMALL", 3: "RS_ERR_CUDA",
                 4: "RS_ERR_TIMEOUT", 5: "RS_ERR_UNSUPPORTED"}
 RS_MODE_AUTO, RS_MODE_LSD, RS_MODE_MSD = 0, 1, 2
+# key kinds (rs_plan.key_kind): how 32-bit key words are ordered
+RS_KEY_U32, RS_KEY_I32, RS_KEY_F32 = 0, 1, 2
 RS_NOALLOC_MAX_KEYS = 1 << 20
 
 
@@ -48,7 +50,7 @@ class RsTraceEntry(ctypes.Structure):
 
 class RsPlan(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_uint32), ("mode", ctypes.c_uint32),
-                ("tile", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("tile", ctypes.c_uint32), ("key_kind", ctypes.c_uint32)]
 
 
 _P = ctypes.c_void_p
@@ -128,7 +130,7 @@ def _plan(plan) -> ctypes.POINTER(RsPlan) | None:
     if isinstance(plan, RsPlan):
         return ctypes.pointer(plan)
     return ctypes.pointer(RsPlan(int(plan.get("digit_bits", 0)), int(plan.get("mode", 0)),
-                                 int(plan.get("tile", 0)), 0))
+                                 int(plan.get("tile", 0)), int(plan.get("key_kind", 0))))
 
 
 def _temp(temp):
@@ -244,9 +246,12 @@ def part_offsets(n: int, num_parts: int = 64) -> np.ndarray:
     return np.array([p * q + min(p, r) for p in range(num_parts + 1)], dtype=np.uint64)
 
 
-def _empty_u32(n, device):
+def _empty_u32(n, device, like=None):
+    """An output buffer of n 32-bit words (the input's dtype when given:
+    int32 storage of uint32 keys, or float32 / int32 keys of another kind)."""
     import torch
-    return torch.empty(max(n, 0), dtype=torch.int32, device=device)
+    dtype = like.dtype if like is not None and like.element_size() == 4 else torch.int32
+    return torch.empty(max(n, 0), dtype=dtype, device=device)
 
 
 def temp_bytes(n: int, pairs: bool = False, plan=None) -> int:
@@ -261,10 +266,11 @@ def _alloc_temp(nbytes: int, device):
 
 
 def sort(keys, num_parts: int = 64, plan=None, out=None, temp=None, stream=None):
-    """Sorted copy of a CUDA tensor of uint32 keys (int32/uint32 storage) and
-    the host partition offsets."""
+    """Sorted copy of a CUDA tensor of 32-bit keys (uint32 in int32 storage by
+    default; plan={"key_kind": RS_KEY_I32 or RS_KEY_F32} for signed or float
+    keys) and the host partition offsets."""
     n = keys.numel()
-    out = _empty_u32(n, keys.device) if out is None else out
+    out = _empty_u32(n, keys.device, keys) if out is None else out
     if temp is None:
         temp = _alloc_temp(rs_sort_u32(None, None, n, plan=plan), keys.device)
     offs = rs_sort_u32(keys, out, n, num_parts, plan, temp, stream)
@@ -274,8 +280,8 @@ def sort(keys, num_parts: int = 64, plan=None, out=None, temp=None, stream=None)
 def sort_pairs(keys, vals, num_parts: int = 64, plan=None, out_keys=None, out_vals=None, temp=None,
                stream=None):
     n = keys.numel()
-    ko = _empty_u32(n, keys.device) if out_keys is None else out_keys
-    vo = _empty_u32(n, keys.device) if out_vals is None else out_vals
+    ko = _empty_u32(n, keys.device, keys) if out_keys is None else out_keys
+    vo = _empty_u32(n, keys.device, vals) if out_vals is None else out_vals
     if temp is None:
         temp = _alloc_temp(rs_sort_u32_pairs(None, None, None, None, n, plan=plan), keys.device)
     offs = rs_sort_u32_pairs(keys, vals, ko, vo, n, num_parts, plan, temp, stream)
@@ -291,8 +297,8 @@ def sort_segmented(keys, vals, seg_offsets_host, num_parts: int = 64, plan=None,
     total = int(h[-1]) if h.size else 0
     dev = keys.device
     d_seg = torch.from_numpy(h.view(np.int64)).to(dev)
-    ko = _empty_u32(total, dev)
-    vo = _empty_u32(total, dev) if vals is not None else None
+    ko = _empty_u32(total, dev, keys)
+    vo = _empty_u32(total, dev, vals) if vals is not None else None
     po = torch.empty(num_segs * (num_parts + 1), dtype=torch.int64, device=dev) if want_part_offsets else None
     if temp is None:
         nb = rs_sort_u32_segmented(None, vals, None, vo, None, h, num_segs, total, num_parts, plan=plan)

@@ -67,8 +67,9 @@ rs_status device_state(DeviceState** out) {
         RS_CUDA(cudaFuncSetAttribute(ks[i].func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks[i].smem)),
                 "cudaFuncSetAttribute(onesweep)");
       const HistKernel* h = hist_kernel(r);
-      RS_CUDA(cudaFuncSetAttribute(h->func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
-              "cudaFuncSetAttribute(hist)");
+      for (const void* f : {h->func, h->func_xf})
+        RS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
+                "cudaFuncSetAttribute(hist)");
     }
     const SegKernels* sk = seg_kernels();
     const void* fn[7] = {sk->pass_keys,  sk->pass_pairs,  sk->tiny_keys, sk->tiny_pairs,
@@ -143,6 +144,7 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 
 // ---- plan -------------------------------------------------------------------
 struct SortPlan {
+  KeyXform xf = kIdentityXform;  // order map of the plan's key kind
   int R = 11;
   bool msd = false;  // top-digit bucketing pass, then the segmented pipeline per bucket
   int nd = 0;
@@ -188,7 +190,19 @@ rs_status pick_kernel(int R, uint32_t tile_idx, bool pairs, bool wide, const One
               wide ? "64-bit" : "32-bit");
 }
 
+// The order map of a key kind (see KeyXform).
+rs_status key_xform(const rs_plan* user, KeyXform* out) {
+  const uint32_t kind = user ? user->key_kind : uint32_t(RS_KEY_U32);
+  switch (kind) {
+    case RS_KEY_U32: *out = KeyXform{0u, 0u}; return RS_OK;
+    case RS_KEY_I32: *out = KeyXform{0u, 0x80000000u}; return RS_OK;
+    case RS_KEY_F32: *out = KeyXform{0x7fffffffu, 0x80000000u}; return RS_OK;
+    default: return fail(RS_ERR_INVALID, "unknown key_kind %u", kind);
+  }
+}
+
 rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p) {
+  if (rs_status st = key_xform(user, &p->xf); st != RS_OK) return st;
   const uint32_t bits = (user && user->digit_bits) ? user->digit_bits : uint32_t(default_digit_bits(n, pairs));
   if (bits != 8 && bits != 11) return fail(RS_ERR_UNSUPPORTED, "digit_bits must be 8 or 11 (got %u)", bits);
   if (user && user->mode > RS_MODE_MSD) return fail(RS_ERR_INVALID, "unknown mode %u", user->mode);
@@ -287,6 +301,7 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
   ha.hist = hist;
   ha.zero_ptr = reinterpret_cast<uint4*>(temp + L.status);
   ha.zero_vec4 = L.status_bytes / 16;
+  ha.xform = p.xf;
   const HistKernel* hk = hist_kernel(p.R);
   const size_t work = (size_t(n) + 4095) / 4096;  // one block per 4096 keys at least
   unsigned hgrid = unsigned(ds->num_sms) * (hk->threads >= 1024 ? 1 : 2);
@@ -315,6 +330,8 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
     pa.status = temp + L.status;
     pa.tile_counter = ctrl + j;
     pa.err = ds->err;
+    pa.xin = p.xf;   // the first executed pass maps the input keys
+    pa.xout = p.xf;  // the last one maps them back
     RS_CUDA(traced(p.R == 8 ? T_PASS8 : T_PASS11, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }),
             "launch onesweep");
   }
@@ -370,7 +387,7 @@ SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int n
 
 rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t* kin, const uint32_t* vin,
                         uint32_t* kout, uint32_t* vout, const uint64_t* seg_off, uint32_t num_segs, int nd,
-                        DeviceState* ds, cudaStream_t s) {
+                        KeyXform xin, KeyXform xout, DeviceState* ds, cudaStream_t s) {
   const SegKernels* sk = seg_kernels();
   const bool pairs = vin != nullptr;
   uint32_t* counts = reinterpret_cast<uint32_t*>(temp + L.counts);
@@ -403,6 +420,7 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
   ha.seg_hist = reinterpret_cast<uint32_t*>(temp + L.seg_hist);
   ha.status = reinterpret_cast<uint32_t*>(temp + L.status);
   ha.jobs = reinterpret_cast<SegTileJob*>(temp + L.jobs);
+  ha.xform = xin;
   RS_CUDA(traced(T_SEGHIST, 0, s, [&] { return launch_seg_hist(ha, cap(L.tiles_ub, size_t(sms)), s); }),
           "launch seg_hist");
   SegScanArgs sa{ha.seg_hist, reinterpret_cast<uint32_t*>(temp + L.seg_bases), counts, nd};
@@ -430,6 +448,8 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
     ga.tile_counter = counts + SEG_TICKETS + p;
     ga.parity = uint32_t(p & 1) ^ 1u;
     ga.err = ds->err;
+    ga.xin = p == 0 ? xin : kIdentityXform;
+    ga.xout = p == nd - 1 ? xout : kIdentityXform;
     RS_CUDA(traced(T_SEGPASS, 0, s,
                    [&] { return launch_seg_pass(ga, pairs, cap(L.tiles_ub, size_t(sms) * 2), s); }),
             "launch seg_pass");
@@ -444,6 +464,8 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
   la.seg_off = seg_off;
   la.num_digits = nd;
   for (int j = 0; j < nd; ++j) la.dig[j] = dig[j];
+  la.xin = xin;
+  la.xout = xout;
   la.list = pa.tiny_seg;
   la.count = counts + SEG_NUM_TINY;
   RS_CUDA(traced(T_LOCAL, 0, s, [&] { return launch_local_sort(la, false, pairs, cap(num_segs, size_t(sms) * 8), s); }),
@@ -529,6 +551,7 @@ rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in
   ha.num_digits = 1;
   ha.dig[0] = p.dig[top];
   ha.hist = hist + size_t(top) * 256;
+  ha.xform = p.xf;
   ha.zero_ptr = reinterpret_cast<uint4*>(temp + M.base.status);
   ha.zero_vec4 = M.base.status_bytes / 16;
   const size_t work = (size_t(n) + 4095) / 4096;
@@ -554,9 +577,11 @@ rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in
   pa.status = temp + M.base.status;
   pa.tile_counter = ctrl;
   pa.err = ds->err;
+  pa.xin = p.xf;              // the bucket buffer keeps the mapped keys,
+  pa.xout = kIdentityXform;   // the local stage maps them back
   RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }), "launch onesweep (top)");
   RS_CUDA(launch_bases_to_offsets(bases + size_t(top) * 256, 256, n, seg_off, s), "launch bucket offsets");
-  return run_segmented(M.seg, temp, bk, bv, keys_out, vals_out, seg_off, 256, p.nd - 1, ds, s);
+  return run_segmented(M.seg, temp, bk, bv, keys_out, vals_out, seg_off, 256, p.nd - 1, kIdentityXform, p.xf, ds, s);
 }
 
 rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
@@ -741,6 +766,8 @@ rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in
   }
   if (plan && plan->digit_bits && plan->digit_bits != 8)
     return fail(RS_ERR_UNSUPPORTED, "the segmented sort uses 8-bit digits");
+  KeyXform xf;
+  if (rs_status st = key_xform(plan, &xf); st != RS_OK) return st;
   if (needs_wide_status(total_n)) return fail(RS_ERR_UNSUPPORTED, "the segmented sort needs total_n < 2^30 - 2^16");
   (void)max_seg;
   const SegLayout L = make_seg_layout(0, num_segs, total_n, 4, pairs);
@@ -774,7 +801,7 @@ rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in
   }
   if (total_n == 0) return RS_OK;
   return run_segmented(L, static_cast<unsigned char*>(temp), keys_in, pairs ? vals_in : nullptr, keys_out,
-                       pairs ? vals_out : nullptr, d_seg_offsets, num_segs, 4, ds, s);
+                       pairs ? vals_out : nullptr, d_seg_offsets, num_segs, 4, xf, xf, ds, s);
 }
 
 rs_status rs_digit_histograms(const uint32_t* keys, uint64_t n, uint32_t digit_bits, uint32_t* d_hist,

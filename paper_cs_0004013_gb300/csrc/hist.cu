@@ -15,7 +15,7 @@ namespace rs {
 
 // Block-private sub-histograms per digit; warps are spread over COPIES
 // copies to thin out shared-memory atomic collisions on skewed data.
-template <int R, int THREADS, int COPIES>
+template <int R, int THREADS, int COPIES, bool XF>
 __global__ void __launch_bounds__(THREADS) upfront_hist_kernel(const HistArgs a) {
   constexpr int DIGITS = 1 << R;
   extern __shared__ __align__(16) uint32_t sh[];  // [COPIES][num_digits][DIGITS]
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(THREADS) upfront_hist_kernel(const HistArgs a)
   }
   const KeyXform xf = a.xform;
   auto count = [&](uint32_t k) {
-    k = to_ordered(k, xf);
+    if constexpr (XF) k = to_ordered(k, xf);
 #pragma unroll
     for (int j = 0; j < kMaxDigits; ++j)
       if (j < nd) atomicAdd(&my[j * DIGITS + digit_of(k, sft[j], wid[j])], 1u);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(THREADS) upfront_hist_kernel(const HistArgs a)
 // every key has the same digit), so the kernel runs at the speed of its
 // loads.  Copies of one warp-lane position are shared by the block's warps
 // (atomics still needed), 128 KiB of shared memory for four digits.
-template <int THREADS>
+template <int THREADS, bool XF>
 __global__ void __launch_bounds__(THREADS, 1) upfront_hist_lanes_kernel(const HistArgs a) {
   constexpr int BINS = 256;
   extern __shared__ __align__(16) uint32_t sh[];  // [num_digits][256][32]
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(THREADS, 1) upfront_hist_lanes_kernel(const Hi
   }
   const KeyXform xf = a.xform;
   auto count = [&](uint32_t k) {
-    k = to_ordered(k, xf);
+    if constexpr (XF) k = to_ordered(k, xf);
 #pragma unroll
     for (int j = 0; j < kMaxDigits; ++j)
       if (j < nd) atomicAdd(&sh[(j * BINS + digit_of(k, sft[j], wid[j])) * 32 + lane], 1u);
@@ -181,7 +181,8 @@ __global__ void __launch_bounds__((1 << R) < 1024 ? (1 << R) : 1024) digit_scan_
 template <int R, int THREADS, int COPIES>
 static cudaError_t launch_hist(const HistArgs& a, unsigned grid, cudaStream_t s) {
   const size_t smem = size_t(COPIES) * a.num_digits * (1u << R) * 4;
-  upfront_hist_kernel<R, THREADS, COPIES><<<grid, THREADS, smem, s>>>(a);
+  if (is_identity(a.xform)) upfront_hist_kernel<R, THREADS, COPIES, false><<<grid, THREADS, smem, s>>>(a);
+  else upfront_hist_kernel<R, THREADS, COPIES, true><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -195,16 +196,19 @@ static cudaError_t launch_scan(const ScanArgs& a, unsigned grid, cudaStream_t s)
 template <int THREADS>
 static cudaError_t launch_hist_lanes(const HistArgs& a, unsigned grid, cudaStream_t s) {
   const size_t smem = size_t(a.num_digits) * 256 * 32 * 4;
-  upfront_hist_lanes_kernel<THREADS><<<grid, THREADS, smem, s>>>(a);
+  if (is_identity(a.xform)) upfront_hist_lanes_kernel<THREADS, false><<<grid, THREADS, smem, s>>>(a);
+  else upfront_hist_lanes_kernel<THREADS, true><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 // Shared memory: 11-bit digits, 3 digits, 2 copies = 48 KiB; 8-bit digits,
 // 4 digits x 256 bins x 32 lane copies = 128 KiB (one block per SM).
 static const HistKernel kHist11 = {11, 512, size_t(2) * 3 * 2048 * 4, &launch_hist<11, 512, 2>,
-                                   reinterpret_cast<const void*>(&upfront_hist_kernel<11, 512, 2>)};
+                                   reinterpret_cast<const void*>(&upfront_hist_kernel<11, 512, 2, false>),
+                                   reinterpret_cast<const void*>(&upfront_hist_kernel<11, 512, 2, true>)};
 static const HistKernel kHist8 = {8, 1024, size_t(4) * 256 * 32 * 4, &launch_hist_lanes<1024>,
-                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024>)};
+                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024, false>),
+                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024, true>)};
 static const ScanKernel kScan11 = {11, 1024, &launch_scan<11>};
 static const ScanKernel kScan8 = {8, 256, &launch_scan<8>};
 

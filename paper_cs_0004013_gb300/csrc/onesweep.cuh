@@ -37,6 +37,8 @@
 //     of the digit in earlier tiles) + (position within the digit here).
 #pragma once
 
+#include <type_traits>
+
 #include "rs_device.cuh"
 #include "rs_internal.h"
 
@@ -313,7 +315,8 @@ struct TileJob {
 template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, bool EARLY_LB>
 __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t* kin, uint32_t* kout,
                                               const uint32_t* vin, uint32_t* vout, uint32_t shift, uint32_t width,
-                                              S* status, uint32_t parity, uint32_t* err, unsigned char* smem) {
+                                              S* status, uint32_t parity, uint32_t* err, KeyXform xin, KeyXform xout,
+                                              unsigned char* smem) {
   using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
   constexpr int DIGITS = L::DIGITS, WARPS = L::WARPS, TILE = L::TILE;
   constexpr int DTH = L::DTH, DPT = L::DPT;
@@ -334,6 +337,10 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   if (valid == TILE) {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) key[j] = ld_stream(kin + wbase + j * 32);
+    if (!is_identity(xin)) {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) key[j] = to_ordered(key[j], xin);
+    }
   } else {
     // Keys past the end act as 0xFFFFFFFF: their digit is the largest and
     // they come after every real key, so they sort to the tile's tail and
@@ -341,7 +348,7 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const size_t idx = wbase + j * 32;
-      key[j] = idx < wend ? kin[idx] : 0xffffffffu;
+      key[j] = idx < wend ? to_ordered(kin[idx], xin) : 0xffffffffu;
     }
   }
 
@@ -450,21 +457,28 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   // 6. write out in tile order: runs of one digit go to consecutive
   // addresses.  The range check only guards against a corrupted offset (it
   // raises an error bit instead of writing out of bounds).
+  // Keys leave through the inverse of the order map when this pass writes
+  // the final order (the loop is written twice so that the identity case
+  // pays nothing).
   bool oob = false;
+  auto write_out = [&](auto invert) {
 #pragma unroll
-  for (int k = 0; k < ITEMS; ++k) {
-    const uint32_t i = k * THREADS + tid;
-    if (valid == TILE || i < valid) {
-      const uint32_t kk = s_buf[i];
-      const uint32_t g = s_goff[digit_of(kk, shift, width)] + i;
-      if (g >= job.out_start && g < job.out_end) {
-        kout[g] = kk;
-        if constexpr (PAIRS) vout[g] = s_buf[TILE + i];
-      } else {
-        oob = true;
+    for (int k = 0; k < ITEMS; ++k) {
+      const uint32_t i = k * THREADS + tid;
+      if (valid == TILE || i < valid) {
+        const uint32_t kk = s_buf[i];
+        const uint32_t g = s_goff[digit_of(kk, shift, width)] + i;
+        if (g >= job.out_start && g < job.out_end) {
+          kout[g] = decltype(invert)::value ? from_ordered(kk, xout) : kk;
+          if constexpr (PAIRS) vout[g] = s_buf[TILE + i];
+        } else {
+          oob = true;
+        }
       }
     }
-  }
+  };
+  if (is_identity(xout)) write_out(std::false_type{});
+  else write_out(std::true_type{});
   if (oob) atomicOr(err, kErrBounds);
 }
 
@@ -506,7 +520,9 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   job.out_end = a.n;
   job.bases = a.bases;
   onesweep_tile<R, THREADS, ITEMS, PAIRS, S, EARLY_LB>(job, kin, kout, vin, vout, a.shift, a.width,
-                                                        reinterpret_cast<S*>(a.status), route.parity, a.err, smem);
+                                                        reinterpret_cast<S*>(a.status), route.parity, a.err,
+                                                        route.src == BUF_IN ? a.xin : KeyXform{0u, 0u},
+                                                        route.last ? a.xout : KeyXform{0u, 0u}, smem);
 }
 
 template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>

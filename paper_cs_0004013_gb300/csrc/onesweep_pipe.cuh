@@ -114,6 +114,9 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_pipe_kernel(const Pass
   const uint32_t num_tiles = uint32_t((size_t(a.n) + TILE - 1) / TILE);
   S* status = reinterpret_cast<S*>(a.status);
   const uint32_t shift = a.shift, width = a.width, parity = route.parity;
+  // order map of the keys read from the input / written as the final order
+  const KeyXform xin = route.src == BUF_IN ? a.xin : KeyXform{0u, 0u};
+  const KeyXform xout = route.last ? a.xout : KeyXform{0u, 0u};
 
   auto clear_tables = [&]() {
     uint4* c4 = reinterpret_cast<uint4*>(smem);
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_pipe_kernel(const Pass
     const size_t wbase = base + size_t(warp) * 32 * ITEMS + lane;
     if (base + TILE <= size_t(a.n)) {
 #pragma unroll
-      for (int j = 0; j < ITEMS; ++j) key[j] = ld_stream(kin + wbase + j * 32);
+      for (int j = 0; j < ITEMS; ++j) key[j] = to_ordered(ld_stream(kin + wbase + j * 32), xin);
       if constexpr (PAIRS) {
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(vin + wbase + j * 32);
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_pipe_kernel(const Pass
 #pragma unroll
       for (int j = 0; j < ITEMS; ++j) {
         const size_t idx = wbase + j * 32;
-        key[j] = idx < a.n ? kin[idx] : 0xffffffffu;
+        key[j] = idx < a.n ? to_ordered(kin[idx], xin) : 0xffffffffu;
         if constexpr (PAIRS) val[j] = idx < a.n ? vin[idx] : 0u;
       }
     }
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_pipe_kernel(const Pass
         const uint32_t kk = buf[i];
         const uint32_t g = goff[digit_of(kk, shift, width)] + i;
         if (g < a.n) {
-          kout[g] = kk;
+          kout[g] = from_ordered(kk, xout);
           if constexpr (PAIRS) vout[g] = buf[TILE + i];
         } else {
           oob = true;

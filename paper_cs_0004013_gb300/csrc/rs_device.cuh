@@ -37,7 +37,7 @@ __device__ __forceinline__ uint32_t to_ordered(uint32_t k, KeyXform x) {
 __device__ __forceinline__ uint32_t from_ordered(uint32_t t, KeyXform x) {
   return t ^ ((uint32_t(~int32_t(t) >> 31) & x.fmask) ^ x.smask);
 }
-__device__ __forceinline__ bool is_identity(KeyXform x) { return (x.fmask | x.smask) == 0u; }
+__host__ __device__ __forceinline__ bool is_identity(KeyXform x) { return (x.fmask | x.smask) == 0u; }
 
 // Digit of `width` bits at `shift` (width >= 1, shift + width <= 32).
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t shift, uint32_t width) {
@@ -155,6 +155,7 @@ enum : int { BUF_IN = 0, BUF_OUT = 1, BUF_ALT = 2 };
 struct Route {
   int active;
   int src, dst;
+  int last;  // the last executed pass (it writes the final order into keys_out)
   uint32_t parity;
 };
 
@@ -180,9 +181,11 @@ __device__ __forceinline__ Route route_of(const uint32_t* skip, int pass, int nu
   r.active = idx >= 0;
   if (!r.active) {
     r.src = r.dst = BUF_IN;
+    r.last = 0;
     r.parity = 0;
     return r;
   }
+  r.last = idx == m - 1;
   r.dst = ((m - 1 - idx) % 2 == 0) ? BUF_OUT : BUF_ALT;
   r.src = idx == 0 ? BUF_IN : (((m - idx) % 2 == 0) ? BUF_OUT : BUF_ALT);
   r.parity = uint32_t(idx & 1) ^ 1u;

@@ -86,7 +86,8 @@ struct HistKernel {
   int threads;
   size_t smem;
   cudaError_t (*launch)(const HistArgs&, unsigned grid, cudaStream_t);
-  const void* func;
+  const void* func;     // the instance for unsigned keys
+  const void* func_xf;  // the instance that maps keys of another kind first
 };
 
 struct ScanKernel {

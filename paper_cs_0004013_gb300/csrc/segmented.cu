@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
     sft[j] = a.dig[j].shift;
     wid[j] = a.dig[j].width;
   }
+  const KeyXform xf = a.xform;
   // sums a segment's lane copies into its global histograms and zeroes them;
   // each thread owns whole (digit, bin) rows and starts at its own lane, so
   // that a warp's reads spread over all banks
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
         if (i0 + uint64_t(u) * THREADS >= end) break;
 #pragma unroll
         for (int j = 0; j < kMaxDigits; ++j)
-          if (j < nd) atomicAdd(&sh[(j * 256 + digit_of(k[u], sft[j], wid[j])) * 32 + lane], 1u);
+          if (j < nd) atomicAdd(&sh[(j * 256 + digit_of(to_ordered(k[u], xf), sft[j], wid[j])) * 32 + lane], 1u);
       }
     }
     // this tile's chained-scan status row starts out "not ready"
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(THREADS, MINB) seg_pass_kernel(const SegPassAr
     job.out_end = jb.out_end;
     job.bases = a.seg_bases + (size_t(jb.li) * a.num_digits + a.pass) * 256;
     onesweep_tile<8, THREADS, ITEMS, PAIRS, uint32_t, false>(job, a.kin, a.kout, a.vin, a.vout, a.shift, a.width,
-                                                              a.status, a.parity, a.err, smem);
+                                                              a.status, a.parity, a.err, a.xin, a.xout, smem);
     __syncthreads();  // the next tile reuses shared memory
   }
 }
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(THREADS, 1) local_sort_kernel(const LocalArgs 
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const uint32_t i = wofs + j * 32;
-      key[j] = i < m ? a.kin[start + i] : 0xffffffffu;
+      key[j] = i < m ? to_ordered(a.kin[start + i], a.xin) : 0xffffffffu;
       if constexpr (PAIRS) val[j] = i < m ? a.vin[start + i] : 0u;
     }
     for (int p = 0; p < a.num_digits; ++p) {
@@ -288,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1) local_sort_kernel(const LocalArgs 
     }
     // the staging buffer holds the sorted segment (then the padding)
     for (uint32_t i = tid; i < m; i += THREADS) {
-      a.kout[start + i] = s_buf[i];
+      a.kout[start + i] = from_ordered(s_buf[i], a.xout);
       if constexpr (PAIRS) a.vout[start + i] = s_buf[TILE + i];
     }
     __syncthreads();

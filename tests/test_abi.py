@@ -50,7 +50,8 @@ def test_temp_queries_grow_with_n_and_payload():
         assert r.rs_sort_u32(None, None, 1 << 20, plan={"digit_bits": bits}) > 0
 
 
-@pytest.mark.parametrize("call", ["n_too_big", "bad_bits", "bad_parts", "msd_pending", "bad_tile"])
+@pytest.mark.parametrize("call", ["n_too_big", "bad_bits", "bad_parts", "msd_pending", "bad_tile", "bad_kind",
+                                  "bad_kind_segmented"])
 def test_invalid_arguments(call):
     import paper_cs_0004013_gb300 as r
     with pytest.raises(r.RsError) as e:
@@ -62,6 +63,12 @@ def test_invalid_arguments(call):
             r.rs_sort_u32(None, None, 10, num_parts=0)
         elif call == "msd_pending":
             r.rs_sort_u32(None, None, 100, plan={"mode": 99})
+        elif call == "bad_kind":
+            r.rs_sort_u32_pairs(None, None, None, None, 100, plan={"key_kind": 3})
+        elif call == "bad_kind_segmented":
+            import numpy as np
+            r.rs_sort_u32_segmented(None, None, None, None, None, np.array([0, 100], np.uint64), 1, 100,
+                                    plan={"key_kind": 9})
         else:
             r.rs_sort_u32(None, None, 100, plan={"tile": 42})
     assert r.rs_last_error() != ""

@@ -336,3 +336,84 @@ def test_planted_offset_and_base_mistakes_are_caught():
         check_offsets(_mut_offsets_upper, 10, 4)
     h = oracle.digit_histograms(np.array([13, 6, 9, 2, 14, 5], np.uint32), [(0, 2)])[0]
     assert list(_mut_bases_inclusive(h)) != read_golden_radix()["base0"]
+
+
+# ------------------------------------------------------------ key kinds
+def read_golden_key_kinds():
+    rows = []
+    with open(os.path.join(GOLDEN, "key_kinds.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            kind, a, b = (part.strip() for part in line.split(";"))
+            rows.append((kind, np.array([int(x, 16) for x in a.split()], np.uint32),
+                         np.array([int(x, 16) for x in b.split()], np.uint32)))
+    return rows
+
+
+def test_golden_key_kinds():
+    for kind, words, want in read_golden_key_kinds():
+        assert np.array_equal(oracle.sort_keys(words, kind), want), kind
+
+
+def _random_words(n, seed):
+    return synth.splitmix64(seed, n).astype(np.uint64).view(np.uint32)[::2].copy()
+
+
+def test_i32_order_is_python_integer_order():
+    w = np.concatenate([_random_words(3000, 5), np.array([0, 1, 0xFFFFFFFF, 0x80000000, 0x7FFFFFFF], np.uint32)])
+    w = np.concatenate([w, w[:500]])  # duplicates
+    ints = [int(x) - (1 << 32) if x >= 1 << 31 else int(x) for x in w]
+    want = sorted(range(len(ints)), key=lambda i: ints[i])  # Python's sort is stable
+    assert np.array_equal(oracle.order_perm(w, "i32"), np.array(want))
+
+
+def _floats_without_nan_or_signed_zero(n, seed):
+    w = _random_words(n, seed)
+    keep = ((w & np.uint32(0x7F800000)) != np.uint32(0x7F800000)) | ((w & np.uint32(0x007FFFFF)) == 0)  # no NaN
+    keep &= (w & np.uint32(0x7FFFFFFF)) != 0  # no zero of either sign
+    w = w[keep]
+    return np.concatenate([w, w[: w.size // 4], np.array([0x7F800000, 0xFF800000], np.uint32)])
+
+
+def test_f32_order_is_numeric_order_off_nan_and_zero():
+    """Away from NaNs and zeros, totalOrder is the numeric order of the
+    values (numpy's float comparison), ties kept in input order."""
+    w = _floats_without_nan_or_signed_zero(5000, 6)
+    want = np.argsort(w.view(np.float32), kind="stable")
+    assert np.array_equal(oracle.order_perm(w, "f32"), want)
+
+
+def test_f32_order_sign_nan_and_zero_rules():
+    w = _random_words(20000, 7)  # about 0.4 % NaNs of each sign
+    w = np.concatenate([w, np.array([0x00000000, 0x80000000, 0x7F800000, 0xFF800000], np.uint32)])
+    s = oracle.sort_keys(w, "f32")
+    neg = (s >> np.uint32(31)).astype(bool)
+    assert not np.any(~neg[:-1] & neg[1:]), "a word with the sign bit set after one without"
+    f = s.view(np.float32)
+    nan = np.isnan(f)
+    # negative NaNs first, positive NaNs last, -0 right before +0
+    first_num = int(np.argmax(~nan))
+    assert np.all(nan[:first_num]) and np.all(neg[:first_num])
+    last_num = len(s) - int(np.argmax(~nan[::-1]))
+    assert np.all(nan[last_num:]) and not np.any(neg[last_num:])
+    iz = int(np.flatnonzero(s == np.uint32(0x80000000))[0])
+    assert s[iz + 1] == 0 and not np.any(f[:iz][~nan[:iz]] > 0)
+
+
+def _mut_f32_magnitudes_not_reversed(w):
+    negative = (w >> np.uint32(31)).astype(bool)
+    magnitude = (w & np.uint32(0x7FFFFFFF)).astype(np.int64)
+    return np.lexsort((magnitude, np.where(negative, 0, 1)))
+
+
+def _mut_f32_as_unsigned(w):
+    return np.argsort(w, kind="stable")
+
+
+@pytest.mark.parametrize("mut", [_mut_f32_magnitudes_not_reversed, _mut_f32_as_unsigned])
+def test_planted_f32_mistakes_are_caught(mut):
+    w = _floats_without_nan_or_signed_zero(5000, 6)
+    assert not np.array_equal(mut(w), np.argsort(w.view(np.float32), kind="stable"))
+    golden = [(k, a, b) for k, a, b in read_golden_key_kinds() if k == "f32"]
+    assert any(not np.array_equal(a[mut(a)], b) for _, a, b in golden)
