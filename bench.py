@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--pairs", action="store_true", help="time key+payload sorts as the main value")
+    ap.add_argument("--keys64", action="store_true", help="64-bit keys (rs_sort_u64), uniform over all 2^64 words")
     ap.add_argument("--key-kind", choices=["u32", "i32", "f32"], default="u32",
                     help="how the 32-bit key words are ordered (u32: the headline workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -152,6 +153,8 @@ def workload_keys(n: int, seed: int, key_kind: str) -> np.ndarray:
     import synth
     if key_kind == "u32":
         return synth.uniform31(n, seed)
+    if key_kind == "u64":
+        return synth.splitmix64(seed, n)
     return synth.splitmix64(seed, (n + 1) // 2).view(np.uint32)[:n].copy()
 
 
@@ -260,12 +263,21 @@ def run_ours(args):
 
     dev = torch.device("cuda", torch.cuda.current_device())
     n = args.n
-    keys = workload_keys(n, synth.CONFIG_SEED + 2 + 1000 * rank, args.key_kind)
-    d_keys = torch.from_numpy(keys.view(np.int32)).to(dev)
+    wide = args.keys64
+    if wide:  # uniform 64-bit words
+        keys = workload_keys(n, synth.CONFIG_SEED + 2 + 1000 * rank, "u64")
+        d_keys = torch.from_numpy(keys.view(np.int64)).to(dev)
+    else:
+        keys = workload_keys(n, synth.CONFIG_SEED + 2 + 1000 * rank, args.key_kind)
+        d_keys = torch.from_numpy(keys.view(np.int32)).to(dev)
     d_out = torch.empty_like(d_keys)
     plan = {"digit_bits": args.digit_bits, "tile": args.tile, "key_kind": KEY_KINDS[args.key_kind]}
     pairs = args.pairs
-    if pairs:
+    if wide and pairs:
+        raise SystemExit("--keys64 sorts keys only")
+    if wide:
+        temp = torch.empty(rs.rs_sort_u64(None, None, n, plan=plan), dtype=torch.uint8, device=dev)
+    elif pairs:
         d_vals = torch.arange(n, dtype=torch.int32, device=dev)
         d_vout = torch.empty_like(d_vals)
         temp = torch.empty(rs.rs_sort_u32_pairs(None, None, None, None, n, plan=plan), dtype=torch.uint8,
@@ -275,7 +287,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        if pairs:
+        if wide:
+            rs.rs_sort_u64(d_keys, d_out, n, 64, plan, temp, stream, want_offsets=True)
+        elif pairs:
             rs.rs_sort_u32_pairs(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
         else:
             rs.rs_sort_u32(d_keys, d_out, n, 64, plan, temp, stream, want_offsets=True)
@@ -337,15 +351,18 @@ def run_ours(args):
         if k in trace:
             pass_kind = k
     passes = trace[pass_kind]["launches"] // args.steps if pass_kind else 0
-    bpk = 4 + passes * (16 if pairs else 8)
+    word_bytes = 16 if (pairs or wide) else 8  # per key and pass: read + write of the words moved
+    # 64-bit keys add the split and the join (8 B read + 8 B written each) and
+    # histogram both word planes
+    bpk = (32 + 8 if wide else 4) + passes * word_bytes
     peak, peak_kind = measured_peak()
     roof = None
     if pass_kind:
         tr = trace[pass_kind]
         avg_ms = tr["total_ms"] / tr["launches"]
-        bytes_launch = (16 if pairs else 8) * tr["keys"] / tr["launches"]
+        bytes_launch = word_bytes * tr["keys"] / tr["launches"]
         achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
-        key = f"{pass_kind}_{'pairs' if pairs else 'keys'}_n{n}"
+        key = f"{pass_kind}_{'keys64' if wide else ('pairs' if pairs else 'keys')}_n{n}"
         traffic = traffic_from_profiles("onesweep.cuh", key)
         roof = {"bound": "hbm", "kernel": pass_kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -360,7 +377,7 @@ def run_ours(args):
     # (the host link carries both directions at once).  The one-stream figure
     # (copy in, sort, copy out, strictly one after another) is reported beside.
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not wide:
         h_in = torch.from_numpy(keys.view(np.int32)).pin_memory()
         h_vin = torch.arange(n, dtype=torch.int32).pin_memory() if pairs else None
         nb = rs.rs_sort_u32_host(None, h_vin, None, h_vin, n, plan=plan)
@@ -409,14 +426,16 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(key_kind=args.key_kind)
+        cpu = cpu_baseline(key_kind="u64" if wide else args.key_kind)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": workload_label(n, pairs, args.key_kind),
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64" if wide else "u32", "data": "synthetic",
+            "config": {"workload": (workload_label(n, pairs, args.key_kind) if not wide else
+                                    workload_label(n, False).replace("uint32 keys uniform in [0, 2^31-1]",
+                                                                     "uint64 keys uniform over all 2^64 values")),
                        "n": n, "digit_bits": args.digit_bits or "auto", "passes": passes,
                        "algorithmic_bytes_per_key": bpk,
                        "sort_roofline_frac": value / world * 1e9 * bpk / (peak * 1e9),

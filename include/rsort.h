@@ -144,6 +144,24 @@ rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in,
                         uint32_t shift, uint32_t width, void* temp,
                         size_t* temp_bytes, rs_stream_t stream);
 
+/* ---- 64-bit keys ------------------------------------------------------- */
+
+/* Sort n 64-bit keys ascending (keys_in, keys_out: DEVICE, n uint64 each,
+ * 8-byte aligned, not overlapping) and write the partition offsets as for
+ * rs_sort_u32.  No counterpart in the paper, whose keys are 32-bit (Sec. 1.1);
+ * the method is the same LSD radix distribution (Sec. 3.3.1) with eight
+ * 8-bit digits.  The keys are split into planes of low and high 32-bit
+ * words; each pass moves both words, the low word serving as the key for
+ * digits 0-3 and the high word for digits 4-7.  plan: digit_bits must be 0
+ * or 8, mode LSD (or 0), tile selects the key+payload tile shape, and
+ * key_kind orders the 64-bit words as unsigned (RS_KEY_U32), two's-complement
+ * signed (RS_KEY_I32) or IEEE-754 binary64 totalOrder (RS_KEY_F32).  Temp:
+ * six n-word planes plus histograms and status.                             */
+rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n,
+                      uint32_t num_parts, uint64_t* h_part_offsets,
+                      const rs_plan* plan, void* temp, size_t* temp_bytes,
+                      rs_stream_t stream);
+
 /* ---- host buffers ------------------------------------------------------- */
 
 /* rs_sort_u32 / rs_sort_u32_pairs on HOST arrays: the keys (and values) are

@@ -65,29 +65,41 @@ def _u32(a) -> np.ndarray:
     return a
 
 
-KINDS = ("u32", "i32", "f32")
+KINDS = ("u32", "i32", "f32", "u64", "i64", "f64")
+
+
+def _words(keys, kind: str) -> np.ndarray:
+    if kind.endswith("64"):
+        a = np.asarray(keys)
+        return a if a.dtype == np.uint64 else a.astype(np.uint64)
+    return _u32(keys)
 
 
 def order_perm(keys, kind: str = "u32") -> np.ndarray:
-    """The stable permutation that puts 32-bit key words in ascending order
-    of their ``kind``:
+    """The stable permutation that puts key words (32- or 64-bit) in
+    ascending order of their ``kind``:
 
-    * ``u32``: unsigned integers (Sec. 1.1);
-    * ``i32``: two's-complement signed integers;
-    * ``f32``: IEEE-754 binary32 values in the totalOrder of IEEE 754-2008
-      Sec. 5.10: a value with the sign bit set comes before one without (so
-      -NaN < -inf < -0 < +0 < +inf < +NaN); among negative ones the larger
-      magnitude (the low 31 bits read as an integer, NaN payloads included)
-      comes first, among non-negative ones the smaller.
+    * ``u32`` / ``u64``: unsigned integers (Sec. 1.1);
+    * ``i32`` / ``i64``: two's-complement signed integers;
+    * ``f32`` / ``f64``: IEEE-754 binary32 / binary64 values in the
+      totalOrder of IEEE 754-2008 Sec. 5.10: a value with the sign bit set
+      comes before one without (so -NaN < -inf < -0 < +0 < +inf < +NaN);
+      among negative ones the larger magnitude (the bits below the sign read
+      as an integer, NaN payloads included) comes first, among non-negative
+      ones the smaller.
     """
-    w = _u32(keys)
-    if kind == "u32":
+    w = _words(keys, kind)
+    if kind in ("u32", "u64"):
         return np.argsort(w, kind="stable")
     if kind == "i32":
         return np.argsort(w.view(np.int32), kind="stable")
-    if kind == "f32":
-        negative = (w >> np.uint32(31)).astype(bool)
-        magnitude = (w & np.uint32(0x7FFFFFFF)).astype(np.int64)
+    if kind == "i64":
+        return np.argsort(w.view(np.int64), kind="stable")
+    if kind in ("f32", "f64"):
+        bits = 32 if kind == "f32" else 64
+        top = w.dtype.type(bits - 1)
+        negative = (w >> top).astype(bool)
+        magnitude = (w & w.dtype.type((1 << (bits - 1)) - 1)).astype(np.int64)
         within = np.where(negative, -magnitude, magnitude)
         sign_class = np.where(negative, 0, 1)
         return np.lexsort((within, sign_class))  # the last key is the primary one; lexsort is stable
@@ -95,18 +107,18 @@ def order_perm(keys, kind: str = "u32") -> np.ndarray:
 
 
 def sort_keys(keys, kind: str = "u32") -> np.ndarray:
-    """Keys in ascending order of their kind (unsigned by default, Sec. 1.1);
-    the words themselves are returned unchanged."""
+    """Keys in ascending order of their kind (unsigned 32-bit by default,
+    Sec. 1.1); the words themselves are returned unchanged."""
     if kind == "u32":
         return np.sort(_u32(keys), kind="stable")
-    w = _u32(keys)
+    w = _words(keys, kind)
     return w[order_perm(w, kind)]
 
 
 def sort_pairs(keys, vals, kind: str = "u32") -> tuple[np.ndarray, np.ndarray]:
     """(key, value) pairs ordered by key alone; equal keys keep input order
     (Sec. 3.3.1, Sec. 5)."""
-    keys = _u32(keys)
+    keys = _words(keys, kind)
     vals = _u32(vals)
     if keys.shape != vals.shape:
         raise ValueError("keys and vals differ in length")

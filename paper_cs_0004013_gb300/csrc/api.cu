@@ -1,5 +1,6 @@
 // C ABI of librsort (declared in include/rsort.h): argument checks, the
 // radix plan, the layout of the caller's temp buffer and the launches.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -88,12 +89,12 @@ rs_status device_state(DeviceState** out) {
 // ---- tracing -------------------------------------------------------------------
 enum TraceKind {
   T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_SEGPLAN, T_SEGHIST, T_SEGSCAN, T_SEGPASS, T_LOCAL,
-  T_H2D, T_D2H, T_KINDS
+  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_KINDS
 };
 const char* const kTraceNames[T_KINDS] = {"clear",       "upfront_hist", "digit_scan", "onesweep_r8",
                                           "onesweep_r11", "seg_part_offsets", "seg_plan", "seg_hist",
                                           "seg_scan",    "seg_pass",     "local_sort", "copy_h2d",
-                                          "copy_d2h"};
+                                          "copy_d2h",    "split64",      "join64"};
 struct TraceRec {
   int kind;
   double keys;
@@ -636,6 +637,109 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
                  static_cast<unsigned char*>(temp), false, ds, s);
 }
 
+// ---- 64-bit keys -----------------------------------------------------------------
+// Eight 8-bit digits; the key+payload pass kernel moves both words of every
+// key (low word as the key for digits 0-3, high word for digits 4-7).
+struct Layout64 {
+  size_t ctrl = 0;    // [0, 8): tile tickets of the 8 passes; [8, 16): skip flags
+  size_t hist = 0;    // [8][256]
+  size_t bases = 0;   // [8][256]
+  size_t status = 0, status_bytes = 0;
+  size_t plane[6] = {};  // lo/hi words of the input, output and alternate order
+  size_t memset_bytes = 0, total = 0;
+};
+
+Layout64 make_layout64(const SortPlan& p, uint64_t n) {
+  Layout64 L;
+  size_t off = 0;
+  L.ctrl = off;
+  off += kAlign;
+  L.hist = off;
+  off = align_up(off + 8 * 256 * 4);
+  L.memset_bytes = off;
+  L.bases = off;
+  off = align_up(off + 8 * 256 * 4);
+  L.status = off;
+  L.status_bytes = p.num_tiles * 256 * (p.k->wide_status ? 8 : 4);
+  off = align_up(off + L.status_bytes);
+  for (int i = 0; i < 6; ++i) {
+    L.plane[i] = off;
+    off = align_up(off + size_t(n) * 4);
+  }
+  L.total = off;
+  return L;
+}
+
+rs_status key_xform64(const rs_plan* user, KeyXform64* out) {
+  const uint32_t kind = user ? user->key_kind : uint32_t(RS_KEY_U32);
+  switch (kind) {
+    case RS_KEY_U32: *out = KeyXform64{0u, 0u, 0u}; return RS_OK;
+    case RS_KEY_I32: *out = KeyXform64{0u, 0u, 0x80000000u}; return RS_OK;
+    case RS_KEY_F32: *out = KeyXform64{0xffffffffu, 0x7fffffffu, 0x80000000u}; return RS_OK;
+    default: return fail(RS_ERR_INVALID, "unknown key_kind %u", kind);
+  }
+}
+
+rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_in, uint64_t* keys_out, uint32_t n,
+                    KeyXform64 x, unsigned char* temp, DeviceState* ds, cudaStream_t s) {
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + L.ctrl);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(temp + L.hist);
+  uint32_t* bases = reinterpret_cast<uint32_t*>(temp + L.bases);
+  uint32_t* pl[6];
+  for (int i = 0; i < 6; ++i) pl[i] = reinterpret_cast<uint32_t*>(temp + L.plane[i]);
+  uint32_t *lo_in = pl[0], *hi_in = pl[1], *lo_out = pl[2], *hi_out = pl[3], *lo_alt = pl[4], *hi_alt = pl[5];
+  RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, L.memset_bytes, s); }),
+          "cudaMemsetAsync(temp)");
+  const unsigned egrid = unsigned(std::min<size_t>((size_t(n) + 255) / 256, size_t(ds->num_sms) * 8));
+  WideArgs wa{reinterpret_cast<const uint2*>(keys_in), reinterpret_cast<uint2*>(keys_out), lo_in, hi_in, n, x};
+  RS_CUDA(traced(T_SPLIT, n, s, [&] { return launch_split64(wa, egrid, s); }), "launch split64");
+  // the eight digit histograms: four per word plane
+  const HistKernel* hk = hist_kernel(8);
+  const size_t work = (size_t(n) + 4095) / 4096;
+  unsigned hgrid = unsigned(ds->num_sms);
+  if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
+  for (int w = 0; w < 2; ++w) {
+    HistArgs ha{};
+    ha.keys = w == 0 ? lo_in : hi_in;
+    ha.n = n;
+    ha.num_digits = 4;
+    for (int j = 0; j < 4; ++j) ha.dig[j] = DigitSpec{uint32_t(8 * j), 8u};
+    ha.hist = hist + size_t(w) * 4 * 256;
+    ha.zero_ptr = w == 0 ? reinterpret_cast<uint4*>(temp + L.status) : nullptr;
+    ha.zero_vec4 = w == 0 ? L.status_bytes / 16 : 0;
+    RS_CUDA(traced(T_HIST, n, s, [&] { return hk->launch(ha, hgrid, s); }), "launch upfront_hist");
+  }
+  ScanArgs sa{hist, bases, ctrl + 8, n};
+  RS_CUDA(traced(T_SCAN, 0, s, [&] { return scan_kernel(8)->launch(sa, 8u, s); }), "launch digit_scan");
+  for (int j = 0; j < 8; ++j) {
+    const bool high = j >= 4;  // which word carries the digit
+    PassArgs pa{};
+    pa.keys_in = high ? hi_in : lo_in;
+    pa.keys_out = high ? hi_out : lo_out;
+    pa.keys_alt = high ? hi_alt : lo_alt;
+    pa.vals_in = high ? lo_in : hi_in;
+    pa.vals_out = high ? lo_out : hi_out;
+    pa.vals_alt = high ? lo_alt : hi_alt;
+    pa.n = n;
+    pa.shift = uint32_t(8 * (j % 4));
+    pa.width = 8;
+    pa.pass = j;
+    pa.num_passes = 8;
+    pa.bases = bases + size_t(j) * 256;
+    pa.skip = ctrl + 8;
+    pa.status = temp + L.status;
+    pa.tile_counter = ctrl + j;
+    pa.err = ds->err;
+    pa.xin = kIdentityXform;   // the planes already hold mapped words
+    pa.xout = kIdentityXform;
+    RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }), "launch onesweep (64-bit)");
+  }
+  // the last executed pass always writes the output planes
+  WideArgs ja{nullptr, reinterpret_cast<uint2*>(keys_out), lo_out, hi_out, n, x};
+  RS_CUDA(traced(T_JOIN, n, s, [&] { return launch_join64(ja, egrid, s); }), "launch join64");
+  return RS_OK;
+}
+
 // Partition offsets of every segment, absolute (segment start added).
 __global__ void seg_part_offsets_kernel(const uint64_t* seg, uint32_t num_segs, uint32_t parts, uint64_t* out) {
   const size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -677,6 +781,48 @@ rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in, ui
                             const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
   return sort_impl(keys_in, vals_in, keys_out, vals_out, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
                    reinterpret_cast<cudaStream_t>(stream), true);
+}
+
+rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t num_parts,
+                      uint64_t* h_part_offsets, const rs_plan* plan, void* temp, size_t* temp_bytes,
+                      rs_stream_t stream) {
+  g_last_error.clear();
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
+  if (n >= (uint64_t(1) << 32)) return fail(RS_ERR_INVALID, "n = %llu: must be below 2^32", (unsigned long long)n);
+  if (num_parts < 1) return fail(RS_ERR_INVALID, "num_parts must be >= 1");
+  if (plan && plan->digit_bits && plan->digit_bits != 8)
+    return fail(RS_ERR_UNSUPPORTED, "64-bit keys use 8-bit digits");
+  if (plan && plan->mode == RS_MODE_MSD) return fail(RS_ERR_UNSUPPORTED, "64-bit keys use the LSD plan");
+  KeyXform64 x;
+  if (rs_status st = key_xform64(plan, &x); st != RS_OK) return st;
+  rs_plan q = plan ? *plan : rs_plan{0, 0, 0, 0};
+  q.digit_bits = 8;
+  q.mode = RS_MODE_LSD;
+  q.key_kind = RS_KEY_U32;
+  SortPlan p;
+  if (rs_status st = make_plan(n, true, &q, &p); st != RS_OK) return st;
+  const Layout64 L = make_layout64(p, n);
+  if (!temp) {
+    *temp_bytes = L.total;
+    return RS_OK;
+  }
+  if (reinterpret_cast<uintptr_t>(temp) % kAlign) return fail(RS_ERR_INVALID, "temp is not 256-byte aligned");
+  if (*temp_bytes < L.total) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, L.total);
+  const size_t nb = size_t(n) * 8;
+  if (n > 0) {
+    if (!keys_in || !keys_out) return fail(RS_ERR_INVALID, "NULL key buffer");
+    if ((reinterpret_cast<uintptr_t>(keys_in) | reinterpret_cast<uintptr_t>(keys_out)) & 7)
+      return fail(RS_ERR_INVALID, "64-bit key buffers must be 8-byte aligned");
+    if (overlaps(keys_out, nb, keys_in, nb)) return fail(RS_ERR_INVALID, "keys_out overlaps keys_in");
+    if (overlaps(keys_out, nb, temp, L.total) || overlaps(keys_in, nb, temp, L.total))
+      return fail(RS_ERR_INVALID, "a key buffer overlaps temp");
+  }
+  if (h_part_offsets) part_offsets_host(n, num_parts, h_part_offsets);
+  if (n == 0) return RS_OK;
+  DeviceState* ds = nullptr;
+  if (rs_status st = device_state(&ds); st != RS_OK) return st;
+  return run_lsd64(p, L, keys_in, keys_out, uint32_t(n), x, static_cast<unsigned char*>(temp), ds, s);
 }
 
 rs_status rs_sort_u32_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in, uint32_t* h_keys_out,

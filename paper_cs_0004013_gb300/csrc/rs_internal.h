@@ -26,6 +26,25 @@ struct KeyXform {
 };
 constexpr KeyXform kIdentityXform = {0u, 0u};
 
+// The same map for 64-bit keys held as (low word, high word): the sign is
+// the high word's top bit; a set sign flips the low word by flo and the high
+// word by fhi, and shi is flipped in the high word of every key.
+// unsigned: (0, 0, 0); signed: (0, 0, 0x80000000); binary64:
+// (0xffffffff, 0x7fffffff, 0x80000000).
+struct KeyXform64 {
+  uint32_t flo, fhi, shi;
+};
+
+// Split of interleaved 64-bit keys into word planes, and the join back.
+struct WideArgs {
+  const uint2* keys;  // split: the input keys
+  uint2* out;         // join: the output keys
+  uint32_t* lo;       // [n] low words
+  uint32_t* hi;       // [n] high words
+  uint64_t n;
+  KeyXform64 x;
+};
+
 // Upfront histogram (one read of the keys, every digit at once) and zeroing
 // of the chained-scan status array.
 struct HistArgs {
@@ -200,6 +219,9 @@ cudaError_t launch_seg_pass(const SegPassArgs& a, bool pairs, unsigned grid, cud
 cudaError_t launch_local_sort(const LocalArgs& a, bool small, bool pairs, unsigned grid, cudaStream_t s);
 cudaError_t launch_bases_to_offsets(const uint32_t* bases, uint32_t num, uint64_t n, uint64_t* seg_off,
                                     cudaStream_t s);
+
+cudaError_t launch_split64(const WideArgs& a, unsigned grid, cudaStream_t s);
+cudaError_t launch_join64(const WideArgs& a, unsigned grid, cudaStream_t s);
 
 // Self-test of the bounded lookback wait (selftest.cu).
 cudaError_t launch_lookback_timeout(const uint32_t* status, uint32_t* err, cudaStream_t s);

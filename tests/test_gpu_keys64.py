@@ -1,0 +1,84 @@
+"""Parity of the 64-bit key sort (rs_sort_u64) with the oracle, bit-exact:
+unsigned, signed and binary64 keys over all 64-bit patterns, digits skipped
+in either word, every key+payload tile shape."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TILE = 8192  # keys per tile of the default key+payload kernel
+KIND = {"u64": 0, "i64": 1, "f64": 2}
+SPECIAL = np.array([0, 1 << 63, 0x7FF0000000000000, 0xFFF0000000000000, 0x7FF8000000000000, 0xFFF8000000000000,
+                    0x7FF0000000000001, 2**64 - 1, 1, (1 << 63) + 1, 0x7FEFFFFFFFFFFFFF, 0xFFEFFFFFFFFFFFFF,
+                    2**63 - 1, 0x3FF0000000000000, 0xBFF0000000000000, 0x00000000FFFFFFFF, 0xFFFFFFFF00000000],
+                   np.uint64)
+
+
+@pytest.fixture(scope="module")
+def rs():
+    import paper_cs_0004013_gb300 as r
+    return r
+
+
+def _words(n, seed):
+    w = synth.splitmix64(seed, n)
+    if n >= SPECIAL.size * 4:
+        pos = (synth.splitmix64(seed + 1, SPECIAL.size * 4) % np.uint64(n)).astype(np.int64)
+        w[pos] = np.tile(SPECIAL, 4)
+    return w
+
+
+def _check(rs, keys, kind, plan=None):
+    import torch
+    d = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    out, offs = rs.sort64(d, plan=dict(plan or {}, key_kind=KIND[kind]))
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), oracle.sort_keys(keys, kind))
+    assert np.array_equal(offs, oracle.partition_offsets(keys.size, 64))
+    assert np.array_equal(d.cpu().numpy().view(np.uint64), keys), "input modified"
+
+
+@pytest.mark.parametrize("kind", ["u64", "i64", "f64"])
+@pytest.mark.parametrize("n", [1, 2, 1000, 3 * TILE + 5, 1 << 20])
+def test_kinds_and_sizes(rs, kind, n):
+    _check(rs, _words(n, 50 + n), kind)
+
+
+@pytest.mark.parametrize("kind", ["u64", "i64", "f64"])
+def test_skipped_digits(rs, kind):
+    n = 200_003
+    r = synth.splitmix64(61, n)
+    _check(rs, r & np.uint64(0xFFFFFFFF), kind)                 # high word constant: its four digits skip
+    _check(rs, r & np.uint64(0xFFFFFFFF00000000), kind)         # low word constant
+    _check(rs, (r & np.uint64(0xFF)) | np.uint64(0xC000000000000000), kind)  # seven digits constant
+    _check(rs, np.full(n, 0xBFF0000000000000, np.uint64), kind)  # every digit skipped: a copy
+
+
+@pytest.mark.parametrize("tile", list(range(1, 14)))
+def test_tile_shapes(rs, tile):
+    plan = {"tile": tile}
+    try:
+        rs.rs_sort_u64(None, None, 1000, plan=plan)
+    except rs.RsError:
+        pytest.skip(f"no key+payload kernel for tile shape {tile}")
+    _check(rs, _words(5 * TILE + 777, 71), "u64", plan)
+
+
+def test_empty_and_offsets_only(rs):
+    import torch
+    d = torch.empty(0, dtype=torch.int64, device="cuda")
+    out, offs = rs.sort64(d)
+    assert out.numel() == 0 and not offs.any()
+
+
+def test_float64_tensor(rs):
+    import torch
+    x = torch.from_numpy(np.linspace(-1e300, 1e300, 100_001)[::-1].copy()).cuda()
+    out, _ = rs.sort64(x, plan={"key_kind": rs.RS_KEY_F32})
+    torch.cuda.synchronize()
+    assert out.dtype == torch.float64
+    assert np.array_equal(out.cpu().numpy(), np.sort(x.cpu().numpy()))

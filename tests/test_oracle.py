@@ -346,8 +346,9 @@ def read_golden_key_kinds():
             if line.startswith("#") or not line.strip():
                 continue
             kind, a, b = (part.strip() for part in line.split(";"))
-            rows.append((kind, np.array([int(x, 16) for x in a.split()], np.uint32),
-                         np.array([int(x, 16) for x in b.split()], np.uint32)))
+            dt = np.uint64 if kind.endswith("64") else np.uint32
+            rows.append((kind, np.array([int(x, 16) for x in a.split()], dt),
+                         np.array([int(x, 16) for x in b.split()], dt)))
     return rows
 
 
@@ -417,3 +418,21 @@ def test_planted_f32_mistakes_are_caught(mut):
     assert not np.array_equal(mut(w), np.argsort(w.view(np.float32), kind="stable"))
     golden = [(k, a, b) for k, a, b in read_golden_key_kinds() if k == "f32"]
     assert any(not np.array_equal(a[mut(a)], b) for _, a, b in golden)
+
+
+def test_i64_order_is_python_integer_order():
+    w = synth.splitmix64(8, 3000)
+    w = np.concatenate([w, w[:400], np.array([0, 1, 2**64 - 1, 2**63, 2**63 - 1], np.uint64)])
+    ints = [int(x) - (1 << 64) if x >= 1 << 63 else int(x) for x in w]
+    want = sorted(range(len(ints)), key=lambda i: ints[i])
+    assert np.array_equal(oracle.order_perm(w, "i64"), np.array(want))
+    assert np.array_equal(oracle.order_perm(w, "u64"), np.array(sorted(range(len(w)), key=lambda i: int(w[i]))))
+
+
+def test_f64_order_is_numeric_order_off_nan_and_zero():
+    w = synth.splitmix64(9, 6000)
+    exp = (w >> np.uint64(52)) & np.uint64(0x7FF)
+    keep = (exp != 0x7FF) & ((w & np.uint64(2**63 - 1)) != 0)
+    w = w[keep]
+    w = np.concatenate([w, w[: w.size // 4], np.array([0x7FF0000000000000, 0xFFF0000000000000], np.uint64)])
+    assert np.array_equal(oracle.order_perm(w, "f64"), np.argsort(w.view(np.float64), kind="stable"))
