@@ -70,7 +70,7 @@ def parse():
                     help="how the 32-bit key words are ordered (u32: the headline workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["plain", "batched", "serve", "dist"], default="plain",
+    ap.add_argument("--workload", choices=["plain", "batched", "serve", "dist", "merge"], default="plain",
                     help="plain: the headline 2^26 sort; batched: 4096 log-uniform segments in one call vs one "
                          "call per array; serve: Poisson request stream; dist: the four skewed 2^26 inputs")
     ap.add_argument("--requests", type=int, default=120, help="requests per load point (serve)")
@@ -649,6 +649,64 @@ def run_dist(args):
     return 0
 
 
+def run_merge(args):
+    """NEXT-4: stable merge of two sorted runs of 2^26 uniform 31-bit keys
+    (the runs sorted by the library first), keys only and with payloads;
+    value = merged keys per second (keys only)."""
+    import torch
+    import synth
+    import paper_cs_0004013_gb300 as rs
+    torch.cuda.set_device(0)
+    n = args.n
+    runs = []
+    for seed in (synth.CONFIG_SEED + 41, synth.CONFIG_SEED + 42):
+        d = torch.from_numpy(synth.uniform31(n, seed).view(np.int32)).cuda()
+        runs.append(rs.sort(d)[0])
+    a, b = runs
+    peak, peak_kind = measured_peak()
+    res = {}
+    for pairs in (False, True):
+        va = torch.arange(n, dtype=torch.int32, device="cuda") if pairs else None
+        vb = torch.arange(n, 2 * n, dtype=torch.int32, device="cuda") if pairs else None
+        out = torch.empty(2 * n, dtype=torch.int32, device="cuda")
+        vout = torch.empty_like(out) if pairs else None
+        temp = torch.empty(rs.rs_merge_u32(None, va, n, None, vb, n, None, vout), dtype=torch.uint8, device="cuda")
+
+        def step():
+            rs.rs_merge_u32(a, va, n, b, vb, n, out, vout, 64, None, temp, want_offsets=True)
+
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = _events()
+        e0.record()
+        for _ in range(args.steps):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        rs.rs_check_device_error()
+        ms = e0.elapsed_time(e1) / args.steps
+        bytes_per_key = 16 if pairs else 8  # read once, written once
+        gbs = 2 * n * bytes_per_key / (ms * 1e-3) / 1e9
+        res["pairs" if pairs else "keys"] = {"gkeys_s": 2 * n / ms / 1e6, "ms": ms, "achieved_gbs": gbs,
+                                             "frac": gbs / peak}
+    sample = slice(None, None, max(1, n // 2048))
+    merged = out.cpu().numpy().view(np.uint32)
+    if not np.all(merged[sample][1:] >= merged[sample][:-1]):
+        raise SystemExit("merged output is not ascending")
+    line = {"metric": METRIC, "value": res["keys"]["gkeys_s"], "unit": "Gkeys/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": res["keys"]["ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": f"stable merge of two sorted runs of {n} uniform 31-bit keys; value = merged "
+                                   "keys per second, keys only", "n_per_run": n},
+            "roofline": {"bound": "hbm", "kernel": "merge", "achieved": res["keys"]["achieved_gbs"], "peak": peak,
+                         "unit": "GB/s", "frac": res["keys"]["frac"], "traffic": None, "peak_kind": peak_kind,
+                         "algorithmic_bytes_per_key": 8},
+            "with_payloads": res["pairs"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -659,6 +717,8 @@ def main():
         return run_serve(args)
     if args.workload == "dist":
         return run_dist(args)
+    if args.workload == "merge":
+        return run_merge(args)
     return run_ours(args)
 
 

@@ -162,6 +162,27 @@ rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n,
                       const rs_plan* plan, void* temp, size_t* temp_bytes,
                       rs_stream_t stream);
 
+/* ---- merging sorted runs ------------------------------------------------- */
+
+/* Stable merge of two runs already sorted in the order of plan->key_kind
+ * (plan may be NULL: unsigned): out[0, na + nb) receives a[0, na) and
+ * b[0, nb) in ascending order, an element of a before an equal one of b, and
+ * the partition offsets of the merged array go to h_part_offsets as for
+ * rs_sort_u32.  The merge at the heart of the paper's cleanup merge-exchange
+ * (Sec. 3.4.2, Sec. 4.6).  a, b, out (and va, vb, vout: all three or none;
+ * an empty run may pass NULL) are DEVICE arrays of uint32 words; outputs must
+ * not overlap inputs.
+ * plan->tile picks the merge tile shape (1..4; 0 = automatic); other plan
+ * fields are ignored.  Runs that are not sorted give an
+ * unspecified order; a tile whose merge path comes out inconsistent is left
+ * unwritten and rs_check_device_error() reports it.  Temp: 4 bytes per tile
+ * of 2816 to 5888 outputs.                                                  */
+rs_status rs_merge_u32(const uint32_t* a, const uint32_t* va, uint64_t na,
+                       const uint32_t* b, const uint32_t* vb, uint64_t nb,
+                       uint32_t* out, uint32_t* vout, uint32_t num_parts,
+                       uint64_t* h_part_offsets, const rs_plan* plan, void* temp,
+                       size_t* temp_bytes, rs_stream_t stream);
+
 /* ---- host buffers ------------------------------------------------------- */
 
 /* rs_sort_u32 / rs_sort_u32_pairs on HOST arrays: the keys (and values) are

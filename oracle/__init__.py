@@ -47,6 +47,7 @@ __all__ = [
     "sort_pairs",
     "partition_offsets",
     "sort_segmented",
+    "merge",
     "digit_plan",
     "digit_of",
     "digit_histograms",
@@ -122,6 +123,18 @@ def sort_pairs(keys, vals, kind: str = "u32") -> tuple[np.ndarray, np.ndarray]:
     vals = _u32(vals)
     if keys.shape != vals.shape:
         raise ValueError("keys and vals differ in length")
+    perm = order_perm(keys, kind)
+    return keys[perm], vals[perm]
+
+
+def merge(a, b, va=None, vb=None, kind: str = "u32"):
+    """The stable merge of two sorted runs: the run a followed by the run b,
+    sorted stably by key (so an element of a precedes an equal one of b).
+    Returns (keys, vals or None)."""
+    keys = np.concatenate([_words(a, kind), _words(b, kind)])
+    if va is None:
+        return keys[order_perm(keys, kind)], None
+    vals = np.concatenate([_u32(va), _u32(vb)])
     perm = order_perm(keys, kind)
     return keys[perm], vals[perm]
 

@@ -24,7 +24,7 @@ __all__ = [
     "rs_sort_u32", "rs_sort_u32_pairs", "rs_sort_u32_segmented", "rs_digit_histograms",
     "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_version", "rs_trace_enable",
     "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS", "rs_selftest_wait_timeout",
-    "rs_sort_u32_host", "rs_sort_u64", "sort64",
+    "rs_sort_u32_host", "rs_sort_u64", "sort64", "rs_merge_u32", "merge",
     "sort", "sort_pairs", "sort_segmented", "temp_bytes", "part_offsets",
     "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD", "RS_KEY_U32", "RS_KEY_I32", "RS_KEY_F32",
 ]
@@ -72,6 +72,7 @@ _SIGS = {
     "rs_trace_enable": [ctypes.c_int],
     "rs_sort_u32_host": [_P, _P, _P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
     "rs_sort_u64": [_P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
+    "rs_merge_u32": [_P, _P, _U64, _P, _P, _U64, _P, _P, _U32, _U64P, _PLANP, _P, _SZP, _P],
     "rs_sort_u32_noalloc": [_P, _P, _U64, _U32, _U64P, _P],
     "rs_selftest_wait_timeout": [_P, ctypes.c_size_t, _P],
     "rs_trace_read": [ctypes.POINTER(RsTraceEntry), _U32, ctypes.POINTER(ctypes.c_uint32)],
@@ -189,6 +190,29 @@ def sort64(keys, num_parts: int = 64, plan=None, out=None, temp=None, stream=Non
         temp = _alloc_temp(rs_sort_u64(None, None, n, plan=plan), keys.device)
     offs = rs_sort_u64(keys, out, n, num_parts, plan, temp, stream)
     return out, offs
+
+
+def rs_merge_u32(a, va, na: int, b, vb, nb: int, out, vout, num_parts: int = 64, plan=None, temp=None,
+                 stream=None, want_offsets: bool = True):
+    """Calls rs_merge_u32; returns as rs_sort_u32."""
+    tp, tb = _temp(temp)
+    offs = np.zeros(num_parts + 1, dtype=np.uint64) if (want_offsets and temp is not None) else None
+    op = offs.ctypes.data_as(_U64P) if offs is not None else None
+    _check(lib.rs_merge_u32(_ptr(a), _ptr(va), na, _ptr(b), _ptr(vb), nb, _ptr(out), _ptr(vout), num_parts, op,
+                            _plan(plan), tp, ctypes.byref(tb), _stream(stream) if temp is not None else None))
+    return tb.value if temp is None else offs
+
+
+def merge(a, b, va=None, vb=None, num_parts: int = 64, plan=None, stream=None):
+    """Stable merge of two sorted CUDA tensors of 32-bit keys (and their
+    payloads): (keys, vals or None, host partition offsets)."""
+    import torch
+    na, nb = a.numel(), b.numel()
+    out = torch.empty(na + nb, dtype=a.dtype, device=a.device)
+    vout = None if va is None else torch.empty(na + nb, dtype=va.dtype, device=a.device)
+    temp = _alloc_temp(rs_merge_u32(None, va, na, None, vb, nb, None, vout, num_parts, plan), a.device)
+    offs = rs_merge_u32(a, va, na, b, vb, nb, out, vout, num_parts, plan, temp, stream)
+    return out, vout, offs
 
 
 def rs_sort_u32_host(h_keys_in, h_vals_in, h_keys_out, h_vals_out, n: int, num_parts: int = 64, plan=None,

@@ -89,12 +89,12 @@ rs_status device_state(DeviceState** out) {
 // ---- tracing -------------------------------------------------------------------
 enum TraceKind {
   T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_SEGPLAN, T_SEGHIST, T_SEGSCAN, T_SEGPASS, T_LOCAL,
-  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_KINDS
+  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_MERGE, T_KINDS
 };
 const char* const kTraceNames[T_KINDS] = {"clear",       "upfront_hist", "digit_scan", "onesweep_r8",
                                           "onesweep_r11", "seg_part_offsets", "seg_plan", "seg_hist",
                                           "seg_scan",    "seg_pass",     "local_sort", "copy_h2d",
-                                          "copy_d2h",    "split64",      "join64"};
+                                          "copy_d2h",    "split64",      "join64",     "merge"};
 struct TraceRec {
   int kind;
   double keys;
@@ -823,6 +823,53 @@ rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, u
   DeviceState* ds = nullptr;
   if (rs_status st = device_state(&ds); st != RS_OK) return st;
   return run_lsd64(p, L, keys_in, keys_out, uint32_t(n), x, static_cast<unsigned char*>(temp), ds, s);
+}
+
+rs_status rs_merge_u32(const uint32_t* a, const uint32_t* va, uint64_t na, const uint32_t* b, const uint32_t* vb,
+                       uint64_t nb, uint32_t* out, uint32_t* vout, uint32_t num_parts, uint64_t* h_part_offsets,
+                       const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
+  g_last_error.clear();
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
+  const uint64_t n = na + nb;
+  if (na >= (uint64_t(1) << 32) || nb >= (uint64_t(1) << 32) || n >= (uint64_t(1) << 32))
+    return fail(RS_ERR_INVALID, "na + nb must be below 2^32");
+  if (num_parts < 1) return fail(RS_ERR_INVALID, "num_parts must be >= 1");
+  // payloads: all three arrays, or none (a run with no elements may pass NULL)
+  const bool pairs = va || vb || vout;
+  if (pairs && ((na && !va) || (nb && !vb) || (na + nb && !vout)))
+    return fail(RS_ERR_INVALID, "va, vb and vout go together");
+  KeyXform x;
+  if (rs_status st = key_xform(plan, &x); st != RS_OK) return st;
+  const uint32_t tile = merge_tile_keys(plan ? plan->tile : 0u, pairs);
+  if (tile == 0) return fail(RS_ERR_UNSUPPORTED, "no merge tile shape %u", plan->tile);
+  const size_t tiles = (size_t(n) + tile - 1) / tile;
+  const size_t need = align_up((tiles + 1) * 4);
+  if (!temp) {
+    *temp_bytes = need;
+    return RS_OK;
+  }
+  if (reinterpret_cast<uintptr_t>(temp) % kAlign) return fail(RS_ERR_INVALID, "temp is not 256-byte aligned");
+  if (*temp_bytes < need) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, need);
+  if ((na && !a) || (nb && !b) || (n && !out)) return fail(RS_ERR_INVALID, "NULL key buffer");
+  if ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(out) |
+       reinterpret_cast<uintptr_t>(va) | reinterpret_cast<uintptr_t>(vb) | reinterpret_cast<uintptr_t>(vout)) & 3)
+    return fail(RS_ERR_INVALID, "buffers must be 4-byte aligned");
+  const void* ins[4] = {a, b, va, vb};
+  const size_t in_n[4] = {size_t(na) * 4, size_t(nb) * 4, size_t(na) * 4, size_t(nb) * 4};
+  for (const void* o : {static_cast<const void*>(out), static_cast<const void*>(vout)}) {
+    for (int i = 0; i < 4; ++i)
+      if (overlaps(o, size_t(n) * 4, ins[i], in_n[i])) return fail(RS_ERR_INVALID, "an output overlaps an input");
+    if (overlaps(o, size_t(n) * 4, temp, need)) return fail(RS_ERR_INVALID, "an output overlaps temp");
+  }
+  if (pairs && overlaps(out, size_t(n) * 4, vout, size_t(n) * 4)) return fail(RS_ERR_INVALID, "out and vout overlap");
+  if (h_part_offsets) part_offsets_host(n, num_parts, h_part_offsets);
+  if (n == 0) return RS_OK;
+  DeviceState* ds = nullptr;
+  if (rs_status st = device_state(&ds); st != RS_OK) return st;
+  MergeArgs m{a, b, va, vb, out, vout, uint32_t(na), uint32_t(nb), static_cast<uint32_t*>(temp), x, ds->err, tile};
+  RS_CUDA(traced(T_MERGE, double(n), s, [&] { return launch_merge(m, s); }), "launch merge");
+  return RS_OK;
 }
 
 rs_status rs_sort_u32_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in, uint32_t* h_keys_out,

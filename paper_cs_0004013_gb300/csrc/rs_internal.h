@@ -220,6 +220,23 @@ cudaError_t launch_local_sort(const LocalArgs& a, bool small, bool pairs, unsign
 cudaError_t launch_bases_to_offsets(const uint32_t* bases, uint32_t num, uint64_t n, uint64_t* seg_off,
                                     cudaStream_t s);
 
+// Stable merge of two sorted runs (merge.cu).
+struct MergeArgs {
+  const uint32_t* a;   // [na] sorted by the order of x
+  const uint32_t* b;   // [nb] sorted by the order of x
+  const uint32_t* va;  // payloads of a, b (both null for keys only)
+  const uint32_t* vb;
+  uint32_t* out;       // [na + nb]
+  uint32_t* vout;
+  uint32_t na, nb;
+  uint32_t* split;     // [tiles + 1] merge-path split of each tile boundary
+  KeyXform x;
+  uint32_t* err;       // device error word
+  uint32_t tile;       // outputs per tile (merge_tile_keys of the chosen shape)
+};
+uint32_t merge_tile_keys(uint32_t shape, bool pairs);
+cudaError_t launch_merge(const MergeArgs& m, cudaStream_t s);
+
 cudaError_t launch_split64(const WideArgs& a, unsigned grid, cudaStream_t s);
 cudaError_t launch_join64(const WideArgs& a, unsigned grid, cudaStream_t s);
 

@@ -436,3 +436,35 @@ def test_f64_order_is_numeric_order_off_nan_and_zero():
     w = w[keep]
     w = np.concatenate([w, w[: w.size // 4], np.array([0x7FF0000000000000, 0xFFF0000000000000], np.uint64)])
     assert np.array_equal(oracle.order_perm(w, "f64"), np.argsort(w.view(np.float64), kind="stable"))
+
+
+# ------------------------------------------------------------ merge
+def _two_pointer_merge(a, b, va, vb, before):
+    """The textbook merge of two sorted lists, taking from a while its head
+    does not come after b's head (``before(x, y)``: x strictly precedes y)."""
+    i = j = 0
+    keys, vals = [], []
+    while i < len(a) or j < len(b):
+        if j >= len(b) or (i < len(a) and not before(b[j], a[i])):
+            keys.append(a[i]); vals.append(va[i]); i += 1
+        else:
+            keys.append(b[j]); vals.append(vb[j]); j += 1
+    return keys, vals
+
+
+@pytest.mark.parametrize("kind", ["u32", "i32"])
+@pytest.mark.parametrize("sizes", [(0, 0), (0, 3), (4, 0), (1, 1), (50, 7), (200, 300)])
+def test_merge_is_the_textbook_merge(kind, sizes):
+    na, nb = sizes
+    a = oracle.sort_keys(synth.uniform31(na, 1) % np.uint32(20), kind) if na else np.zeros(0, np.uint32)
+    b = oracle.sort_keys(synth.uniform31(nb, 2) % np.uint32(20), kind) if nb else np.zeros(0, np.uint32)
+    if kind == "i32":  # negative keys too
+        a = oracle.sort_keys((a.view(np.int32) - 10).view(np.uint32), kind)
+        b = oracle.sort_keys((b.view(np.int32) - 10).view(np.uint32), kind)
+    va = np.arange(na, dtype=np.uint32)
+    vb = np.arange(na, na + nb, dtype=np.uint32)
+    conv = (lambda w: int(np.uint32(w).view(np.int32))) if kind == "i32" else int
+    wk, wv = _two_pointer_merge([conv(x) for x in a], [conv(x) for x in b], list(va), list(vb),
+                                lambda x, y: x < y)
+    ko, vo = oracle.merge(a, b, va, vb, kind)
+    assert [conv(x) for x in ko] == wk and list(vo) == wv
