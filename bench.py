@@ -273,10 +273,14 @@ def run_ours(args):
     d_out = torch.empty_like(d_keys)
     plan = {"digit_bits": args.digit_bits, "tile": args.tile, "key_kind": KEY_KINDS[args.key_kind]}
     pairs = args.pairs
-    if wide and pairs:
-        raise SystemExit("--keys64 sorts keys only")
     if wide:
-        temp = torch.empty(rs.rs_sort_u64(None, None, n, plan=plan), dtype=torch.uint8, device=dev)
+        if pairs:
+            d_vals = torch.arange(n, dtype=torch.int32, device=dev)
+            d_vout = torch.empty_like(d_vals)
+            nb = rs.rs_sort_u64_pairs(None, None, None, None, n, plan=plan)
+        else:
+            nb = rs.rs_sort_u64(None, None, n, plan=plan)
+        temp = torch.empty(nb, dtype=torch.uint8, device=dev)
     elif pairs:
         d_vals = torch.arange(n, dtype=torch.int32, device=dev)
         d_vout = torch.empty_like(d_vals)
@@ -287,7 +291,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        if wide:
+        if wide and pairs:
+            rs.rs_sort_u64_pairs(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
+        elif wide:
             rs.rs_sort_u64(d_keys, d_out, n, 64, plan, temp, stream, want_offsets=True)
         elif pairs:
             rs.rs_sort_u32_pairs(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
@@ -351,7 +357,8 @@ def run_ours(args):
         if k in trace:
             pass_kind = k
     passes = trace[pass_kind]["launches"] // args.steps if pass_kind else 0
-    word_bytes = 16 if (pairs or wide) else 8  # per key and pass: read + write of the words moved
+    # per key and pass: read + write of the words moved
+    word_bytes = 8 * ((2 if wide else 1) + (1 if pairs else 0))
     # 64-bit keys add the split and the join (8 B read + 8 B written each) and
     # histogram both word planes
     bpk = (32 + 8 if wide else 4) + passes * word_bytes
@@ -434,7 +441,7 @@ def run_ours(args):
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64" if wide else "u32", "data": "synthetic",
             "config": {"workload": (workload_label(n, pairs, args.key_kind) if not wide else
-                                    workload_label(n, False).replace("uint32 keys uniform in [0, 2^31-1]",
+                                    workload_label(n, pairs).replace("uint32 keys uniform in [0, 2^31-1]",
                                                                      "uint64 keys uniform over all 2^64 values")),
                        "n": n, "digit_bits": args.digit_bits or "auto", "passes": passes,
                        "algorithmic_bytes_per_key": bpk,

@@ -183,6 +183,15 @@ rs_status rs_merge_u32(const uint32_t* a, const uint32_t* va, uint64_t na,
                        uint64_t* h_part_offsets, const rs_plan* plan, void* temp,
                        size_t* temp_bytes, rs_stream_t stream);
 
+/* rs_sort_u64 with a uint32 value per key (vals_in, vals_out: DEVICE, n
+ * each): stable by key.  Each pass moves three words per key (both key words
+ * and the value); the values go straight from vals_in to vals_out.         */
+rs_status rs_sort_u64_pairs(const uint64_t* keys_in, const uint32_t* vals_in,
+                            uint64_t* keys_out, uint32_t* vals_out, uint64_t n,
+                            uint32_t num_parts, uint64_t* h_part_offsets,
+                            const rs_plan* plan, void* temp, size_t* temp_bytes,
+                            rs_stream_t stream);
+
 /* ---- host buffers ------------------------------------------------------- */
 
 /* rs_sort_u32 / rs_sort_u32_pairs on HOST arrays: the keys (and values) are

@@ -170,23 +170,25 @@ uint32_t default_tile(int R, bool pairs, uint64_t n) {
 // n + one tile must fit the 30-bit count field of 32-bit status words.
 bool needs_wide_status(uint64_t n) { return n + 65536 > uint64_t(StatusCodec<uint32_t>::kVal); }
 
-rs_status pick_kernel(int R, uint32_t tile_idx, bool pairs, bool wide, const OnesweepKernel** out) {
+rs_status pick_kernel(int R, uint32_t tile_idx, int vwords, bool wide, const OnesweepKernel** out) {
   int cnt = 0;
   const OnesweepKernel* ks = R == 8 ? onesweep_kernels_r8(&cnt) : onesweep_kernels_r11(&cnt);
   const int shape = tile_idx == 0 ? 0 : int(tile_idx) - 1;
+  const bool pairs = vwords > 0;
   bool any = false, any_payload = false;
   for (int i = 0; i < cnt; ++i) {
     if (ks[i].shape != shape) continue;
     any = true;
-    any_payload |= ks[i].pairs == pairs;
-    if (ks[i].pairs == pairs && ks[i].wide_status == wide) {
+    any_payload |= ks[i].vwords() == vwords;
+    if (ks[i].vwords() == vwords && ks[i].wide_status == wide) {
       *out = &ks[i];
       return RS_OK;
     }
   }
   if (!any) return fail(RS_ERR_UNSUPPORTED, "tile shape %u not available for %d-bit digits", tile_idx, R);
   if (!any_payload)
-    return fail(RS_ERR_UNSUPPORTED, "tile shape %u has no %s kernel", tile_idx, pairs ? "key+value" : "keys-only");
+    return fail(RS_ERR_UNSUPPORTED, "tile shape %u has no kernel moving %d payload word(s)", tile_idx, vwords);
+  (void)pairs;
   return fail(RS_ERR_UNSUPPORTED, "tile shape %u has no %s-status kernel (n too large for it)", tile_idx,
               wide ? "64-bit" : "32-bit");
 }
@@ -202,7 +204,8 @@ rs_status key_xform(const rs_plan* user, KeyXform* out) {
   }
 }
 
-rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p) {
+// vwords: payload words per key the passes move (-1: 1 for pairs, else 0).
+rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p, int vwords = -1) {
   if (rs_status st = key_xform(user, &p->xf); st != RS_OK) return st;
   const uint32_t bits = (user && user->digit_bits) ? user->digit_bits : uint32_t(default_digit_bits(n, pairs));
   if (bits != 8 && bits != 11) return fail(RS_ERR_UNSUPPORTED, "digit_bits must be 8 or 11 (got %u)", bits);
@@ -221,7 +224,7 @@ rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p) {
   const bool wide = needs_wide_status(n);
   uint32_t tile = (user && user->tile) ? user->tile : default_tile(p->R, pairs, n);
   if (wide && !(user && user->tile)) tile = 1;  // only shape 0 has 64-bit status kernels
-  rs_status st = pick_kernel(p->R, tile, pairs, wide, &p->k);
+  rs_status st = pick_kernel(p->R, tile, vwords >= 0 ? vwords : (pairs ? 1 : 0), wide, &p->k);
   if (st != RS_OK) return st;
   p->num_tiles = (n + p->k->tile - 1) / p->k->tile;
   return RS_OK;
@@ -646,10 +649,11 @@ struct Layout64 {
   size_t bases = 0;   // [8][256]
   size_t status = 0, status_bytes = 0;
   size_t plane[6] = {};  // lo/hi words of the input, output and alternate order
+  size_t val_alt = 0;    // the values' alternate plane (key+value sorts)
   size_t memset_bytes = 0, total = 0;
 };
 
-Layout64 make_layout64(const SortPlan& p, uint64_t n) {
+Layout64 make_layout64(const SortPlan& p, uint64_t n, bool pairs) {
   Layout64 L;
   size_t off = 0;
   L.ctrl = off;
@@ -666,6 +670,10 @@ Layout64 make_layout64(const SortPlan& p, uint64_t n) {
     L.plane[i] = off;
     off = align_up(off + size_t(n) * 4);
   }
+  if (pairs) {
+    L.val_alt = off;
+    off = align_up(off + size_t(n) * 4);
+  }
   L.total = off;
   return L;
 }
@@ -680,8 +688,9 @@ rs_status key_xform64(const rs_plan* user, KeyXform64* out) {
   }
 }
 
-rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_in, uint64_t* keys_out, uint32_t n,
-                    KeyXform64 x, unsigned char* temp, DeviceState* ds, cudaStream_t s) {
+rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_in, const uint32_t* vals_in,
+                    uint64_t* keys_out, uint32_t* vals_out, uint32_t n, KeyXform64 x, unsigned char* temp,
+                    DeviceState* ds, cudaStream_t s) {
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + L.ctrl);
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp + L.hist);
   uint32_t* bases = reinterpret_cast<uint32_t*>(temp + L.bases);
@@ -720,6 +729,11 @@ rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_i
     pa.vals_in = high ? lo_in : hi_in;
     pa.vals_out = high ? lo_out : hi_out;
     pa.vals_alt = high ? lo_alt : hi_alt;
+    if (vals_in) {  // the values ride as a second payload word, from and into the caller's arrays
+      pa.vals2_in = vals_in;
+      pa.vals2_out = vals_out;
+      pa.vals2_alt = reinterpret_cast<uint32_t*>(temp + L.val_alt);
+    }
     pa.n = n;
     pa.shift = uint32_t(8 * (j % 4));
     pa.width = 8;
@@ -783,9 +797,9 @@ rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in, ui
                    reinterpret_cast<cudaStream_t>(stream), true);
 }
 
-rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t num_parts,
-                      uint64_t* h_part_offsets, const rs_plan* plan, void* temp, size_t* temp_bytes,
-                      rs_stream_t stream) {
+static rs_status sort64_impl(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                             uint32_t* vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
+                             const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream, bool pairs) {
   g_last_error.clear();
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
@@ -801,8 +815,8 @@ rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, u
   q.mode = RS_MODE_LSD;
   q.key_kind = RS_KEY_U32;
   SortPlan p;
-  if (rs_status st = make_plan(n, true, &q, &p); st != RS_OK) return st;
-  const Layout64 L = make_layout64(p, n);
+  if (rs_status st = make_plan(n, true, &q, &p, pairs ? 2 : 1); st != RS_OK) return st;
+  const Layout64 L = make_layout64(p, n, pairs);
   if (!temp) {
     *temp_bytes = L.total;
     return RS_OK;
@@ -817,12 +831,37 @@ rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, u
     if (overlaps(keys_out, nb, keys_in, nb)) return fail(RS_ERR_INVALID, "keys_out overlaps keys_in");
     if (overlaps(keys_out, nb, temp, L.total) || overlaps(keys_in, nb, temp, L.total))
       return fail(RS_ERR_INVALID, "a key buffer overlaps temp");
+    if (pairs) {
+      const size_t vb = size_t(n) * 4;
+      if (!vals_in || !vals_out) return fail(RS_ERR_INVALID, "NULL value buffer");
+      if ((reinterpret_cast<uintptr_t>(vals_in) | reinterpret_cast<uintptr_t>(vals_out)) & 3)
+        return fail(RS_ERR_INVALID, "value buffers must be 4-byte aligned");
+      if (overlaps(vals_out, vb, vals_in, vb) || overlaps(vals_out, vb, keys_in, nb) ||
+          overlaps(vals_out, vb, keys_out, nb) || overlaps(vals_out, vb, temp, L.total) ||
+          overlaps(keys_out, nb, vals_in, vb))
+        return fail(RS_ERR_INVALID, "an output overlaps another buffer");
+    }
   }
   if (h_part_offsets) part_offsets_host(n, num_parts, h_part_offsets);
   if (n == 0) return RS_OK;
   DeviceState* ds = nullptr;
   if (rs_status st = device_state(&ds); st != RS_OK) return st;
-  return run_lsd64(p, L, keys_in, keys_out, uint32_t(n), x, static_cast<unsigned char*>(temp), ds, s);
+  return run_lsd64(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n), x,
+                   static_cast<unsigned char*>(temp), ds, s);
+}
+
+rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t num_parts,
+                      uint64_t* h_part_offsets, const rs_plan* plan, void* temp, size_t* temp_bytes,
+                      rs_stream_t stream) {
+  return sort64_impl(keys_in, nullptr, keys_out, nullptr, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
+                     stream, false);
+}
+
+rs_status rs_sort_u64_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
+                            uint32_t* vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
+                            const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
+  return sort64_impl(keys_in, vals_in, keys_out, vals_out, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
+                     stream, true);
 }
 
 rs_status rs_merge_u32(const uint32_t* a, const uint32_t* va, uint64_t na, const uint32_t* b, const uint32_t* vb,

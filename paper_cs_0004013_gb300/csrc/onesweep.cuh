@@ -102,7 +102,9 @@ struct CntVec {
   }
 };
 
-template <int R, int THREADS, int ITEMS, bool PAIRS>
+// NV: payload words moved with every key (0 = keys only, 1 = key + value,
+// 2 = key + two words, e.g. the other half of a 64-bit key and a value).
+template <int R, int THREADS, int ITEMS, int NV>
 struct OnesweepLayout {
   static constexpr int DIGITS = 1 << R;
   static constexpr int WARPS = THREADS / 32;
@@ -115,7 +117,7 @@ struct OnesweepLayout {
   static constexpr size_t MASK_BYTES = size_t(WARPS) * kMaskSlots * 4;
   static constexpr size_t CNT_BYTES = size_t(WARPS) * DIGITS * 2;
   static constexpr size_t RANK_BYTES = MASK_BYTES + CNT_BYTES;
-  static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (PAIRS ? 2 : 1);
+  static constexpr size_t BUF_BYTES = size_t(TILE) * 4 * (1 + NV);
   static constexpr size_t UNION_BYTES = ((RANK_BYTES > BUF_BYTES ? RANK_BYTES : BUF_BYTES) + 15) / 16 * 16;
   static constexpr size_t OFF_GOFF = UNION_BYTES;
   static constexpr size_t OFF_WARP = OFF_GOFF + size_t(DIGITS) * 4;
@@ -312,12 +314,13 @@ struct TileJob {
 
 // One tile of an LSD pass (steps 1-6 above).  The rank tables must be zero
 // on entry (the caller clears them and synchronises the block).
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, bool EARLY_LB>
+template <int R, int THREADS, int ITEMS, int NV, typename S, bool EARLY_LB>
 __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t* kin, uint32_t* kout,
-                                              const uint32_t* vin, uint32_t* vout, uint32_t shift, uint32_t width,
+                                              const uint32_t* vin, uint32_t* vout, const uint32_t* vin2,
+                                              uint32_t* vout2, uint32_t shift, uint32_t width,
                                               S* status, uint32_t parity, uint32_t* err, KeyXform xin, KeyXform xout,
                                               unsigned char* smem) {
-  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
   constexpr int DIGITS = L::DIGITS, WARPS = L::WARPS, TILE = L::TILE;
   constexpr int DTH = L::DTH, DPT = L::DPT;
   // rank tables ([WARPS][kMaskSlots] lane masks, then [WARPS][DIGITS] 16-bit
@@ -432,24 +435,25 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
     else rk[j >> 1] += pos;
   }
   __syncthreads();  // rank tables are dead; the staging buffer reuses them
-  uint32_t val[PAIRS ? ITEMS : 1];
-  if constexpr (PAIRS) {
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) s_buf[(rk[j >> 1] >> (16 * (j & 1))) & 0xffffu] = key[j];
+  // payload words, one at a time (each staged in its own TILE-word section)
+#pragma unroll
+  for (int w = 0; w < NV; ++w) {
+    const uint32_t* src = w == 0 ? vin : vin2;
+    uint32_t val[ITEMS];
     if (valid == TILE) {
 #pragma unroll
-      for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(vin + wbase + j * 32);
+      for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(src + wbase + j * 32);
     } else {
 #pragma unroll
       for (int j = 0; j < ITEMS; ++j) {
         const size_t idx = wbase + j * 32;
-        val[j] = idx < wend ? vin[idx] : 0u;
+        val[j] = idx < wend ? src[idx] : 0u;
       }
     }
-  }
 #pragma unroll
-  for (int j = 0; j < ITEMS; ++j) s_buf[(rk[j >> 1] >> (16 * (j & 1))) & 0xffffu] = key[j];
-  if constexpr (PAIRS) {
-#pragma unroll
-    for (int j = 0; j < ITEMS; ++j) s_buf[TILE + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = val[j];
+    for (int j = 0; j < ITEMS; ++j) s_buf[(1 + w) * TILE + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = val[j];
   }
   if constexpr (!EARLY_LB) do_lookback();
   __syncthreads();
@@ -470,7 +474,8 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
         const uint32_t g = s_goff[digit_of(kk, shift, width)] + i;
         if (g >= job.out_start && g < job.out_end) {
           kout[g] = decltype(invert)::value ? from_ordered(kk, xout) : kk;
-          if constexpr (PAIRS) vout[g] = s_buf[TILE + i];
+          if constexpr (NV >= 1) vout[g] = s_buf[TILE + i];
+          if constexpr (NV >= 2) vout2[g] = s_buf[2 * TILE + i];
         } else {
           oob = true;
         }
@@ -483,9 +488,9 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
 }
 
 // Clears the rank tables and takes the block's tile ticket.
-template <int R, int THREADS, int ITEMS, bool PAIRS>
+template <int R, int THREADS, int ITEMS, int NV>
 __device__ __forceinline__ uint32_t begin_tile(uint32_t* counter, unsigned char* smem) {
-  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
   uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
   uint4* c4 = reinterpret_cast<uint4*>(smem);
   for (int i = threadIdx.x; i < int(L::RANK_BYTES / 16); i += THREADS) c4[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -495,21 +500,25 @@ __device__ __forceinline__ uint32_t begin_tile(uint32_t* counter, unsigned char*
 }
 
 // The plain pass: tile i covers keys [i * TILE, (i + 1) * TILE) of one array.
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
+template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB>
 __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs a) {
-  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
   extern __shared__ __align__(16) unsigned char smem[];
   const Route route = route_of(a.skip, a.pass, a.num_passes);
   if (!route.active) return;
   const uint32_t* kin = route.src == BUF_IN ? a.keys_in : (route.src == BUF_OUT ? a.keys_out : a.keys_alt);
   uint32_t* kout = route.dst == BUF_OUT ? a.keys_out : a.keys_alt;
-  const uint32_t* vin = nullptr;
-  uint32_t* vout = nullptr;
-  if constexpr (PAIRS) {
+  const uint32_t *vin = nullptr, *vin2 = nullptr;
+  uint32_t *vout = nullptr, *vout2 = nullptr;
+  if constexpr (NV >= 1) {
     vin = route.src == BUF_IN ? a.vals_in : (route.src == BUF_OUT ? a.vals_out : a.vals_alt);
     vout = route.dst == BUF_OUT ? a.vals_out : a.vals_alt;
   }
-  const uint32_t tile = begin_tile<R, THREADS, ITEMS, PAIRS>(a.tile_counter, smem);
+  if constexpr (NV >= 2) {
+    vin2 = route.src == BUF_IN ? a.vals2_in : (route.src == BUF_OUT ? a.vals2_out : a.vals2_alt);
+    vout2 = route.dst == BUF_OUT ? a.vals2_out : a.vals2_alt;
+  }
+  const uint32_t tile = begin_tile<R, THREADS, ITEMS, NV>(a.tile_counter, smem);
   TileJob job;
   job.tile = tile;
   job.first = 0;
@@ -519,32 +528,34 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   job.out_start = 0;
   job.out_end = a.n;
   job.bases = a.bases;
-  onesweep_tile<R, THREADS, ITEMS, PAIRS, S, EARLY_LB>(job, kin, kout, vin, vout, a.shift, a.width,
+  onesweep_tile<R, THREADS, ITEMS, NV, S, EARLY_LB>(job, kin, kout, vin, vout, vin2, vout2, a.shift, a.width,
                                                         reinterpret_cast<S*>(a.status), route.parity, a.err,
                                                         route.src == BUF_IN ? a.xin : KeyXform{0u, 0u},
                                                         route.last ? a.xout : KeyXform{0u, 0u}, smem);
 }
 
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
+template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB>
 cudaError_t launch_onesweep(const PassArgs& a, unsigned grid, cudaStream_t s) {
-  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
-  onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB, EARLY_LB><<<grid, THREADS, L::SMEM, s>>>(a);
+  using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
+  onesweep_kernel<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB><<<grid, THREADS, L::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int R, int THREADS, int ITEMS, bool PAIRS, typename S, int MINB, bool EARLY_LB>
+template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB>
 OnesweepKernel make_onesweep(int shape_id) {
-  using L = OnesweepLayout<R, THREADS, ITEMS, PAIRS>;
+  using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
   return OnesweepKernel{R,
                         shape_id,
                         THREADS,
                         ITEMS,
                         L::TILE,
-                        PAIRS,
+                        NV >= 1,
                         sizeof(S) == 8,
                         L::SMEM,
-                        &launch_onesweep<R, THREADS, ITEMS, PAIRS, S, MINB, EARLY_LB>,
-                        reinterpret_cast<const void*>(&onesweep_kernel<R, THREADS, ITEMS, PAIRS, S, MINB, EARLY_LB>)};
+                        &launch_onesweep<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB>,
+                        reinterpret_cast<const void*>(&onesweep_kernel<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB>),
+                        0,
+                        NV};
 }
 
 }  // namespace rs

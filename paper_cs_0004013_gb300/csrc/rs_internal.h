@@ -74,6 +74,9 @@ struct PassArgs {
   const uint32_t* vals_in;
   uint32_t* vals_out;
   uint32_t* vals_alt;
+  const uint32_t* vals2_in;  // a second payload word (kernels with two)
+  uint32_t* vals2_out;
+  uint32_t* vals2_alt;
   uint32_t n;
   uint32_t shift, width;
   int pass, num_passes;
@@ -98,6 +101,8 @@ struct OnesweepKernel {
   cudaError_t (*launch)(const PassArgs&, unsigned grid, cudaStream_t);
   const void* func;  // kernel symbol (for attributes)
   int persistent_per_sm = 0;  // > 0: persistent kernel, grid = SMs x this (capped by tiles)
+  int value_words = -1;       // payload words per key (-1: 1 if pairs else 0)
+  int vwords() const { return value_words >= 0 ? value_words : (pairs ? 1 : 0); }
 };
 
 struct HistKernel {

@@ -82,3 +82,32 @@ def test_float64_tensor(rs):
     torch.cuda.synchronize()
     assert out.dtype == torch.float64
     assert np.array_equal(out.cpu().numpy(), np.sort(x.cpu().numpy()))
+
+
+def _check_pairs(rs, keys, kind, plan=None):
+    import torch
+    vals = np.arange(keys.size, dtype=np.uint32)
+    dk = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    dv = torch.from_numpy(vals.view(np.int32).copy()).cuda()
+    ko, vo, offs = rs.sort64_pairs(dk, dv, plan=dict(plan or {}, key_kind=KIND[kind]))
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk, wv = oracle.sort_pairs(keys, vals, kind)
+    assert np.array_equal(ko.cpu().numpy().view(np.uint64), wk)
+    assert np.array_equal(vo.cpu().numpy().view(np.uint32), wv)
+    assert np.array_equal(offs, oracle.partition_offsets(keys.size, 64))
+
+
+@pytest.mark.parametrize("kind", ["u64", "i64", "f64"])
+@pytest.mark.parametrize("n", [1, 1000, 3 * TILE + 5, 1 << 20])
+def test_pairs(rs, kind, n):
+    _check_pairs(rs, _words(n, 80 + n), kind)
+
+
+@pytest.mark.parametrize("kind", ["u64", "f64"])
+def test_pairs_stable_and_skipped(rs, kind):
+    n = 300_007
+    r = synth.splitmix64(83, n)
+    _check_pairs(rs, r % np.uint64(97) * np.uint64(0x0101010101010101), kind)  # few distinct keys
+    _check_pairs(rs, r & np.uint64(0xFFFF00000000), kind)                    # six digits constant
+    _check_pairs(rs, np.full(n, 0xC000000000000000, np.uint64), kind)        # every digit skipped
