@@ -374,6 +374,17 @@ def run_ours(args):
         roof = {"bound": "hbm", "kernel": pass_kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms}
+        # The resource that binds the pass: shared-memory wavefronts (one per SM
+        # per cycle at most).  Wavefronts per launch come from the same ncu
+        # capture as the traffic; the rate uses this run's launch time and SM clock.
+        waves = traffic_from_profiles("onesweep.cuh", key + "_smem_wavefronts")
+        if waves:
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            csum = clocks.summary()
+            mhz = csum.get("sm_mhz") or csum.get("sm_max_mhz") or 2070.0
+            per_cycle = waves / (avg_ms * 1e-3 * mhz * 1e6 * sms)
+            roof["smem"] = {"wavefronts_per_launch": waves, "achieved_per_sm_cycle": per_cycle,
+                            "peak_per_sm_cycle": 1.0, "frac": per_cycle, "sm_mhz": mhz, "sms": sms}
     launches = sum(v["launches"] for k, v in trace.items() if k != "clear")
 
     # end to end through the C entry for host buffers (rs_sort_u32_host):
