@@ -636,6 +636,26 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   if (p.msd)
     return run_msd(p, M, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
                    static_cast<unsigned char*>(temp), ds, s);
+  // A small array with the automatic plan fits one block: every digit is
+  // sorted in shared memory by one launch (no histogram, scans or tiled
+  // passes), which is several times faster for such sizes.
+  const SegKernels* sk = seg_kernels();
+  const bool automatic = !plan || (plan->digit_bits == 0 && plan->mode == RS_MODE_AUTO && plan->tile == 0);
+  if (automatic && n <= sk->small_max) {
+    LocalArgs la{};
+    la.kin = keys_in;
+    la.kout = keys_out;
+    la.vin = pairs ? vals_in : nullptr;
+    la.vout = pairs ? vals_out : nullptr;
+    la.single_n = uint32_t(n);
+    la.num_digits = 4;
+    for (int j = 0; j < 4; ++j) la.dig[j] = DigitSpec{uint32_t(8 * j), 8u};
+    la.xin = p.xf;
+    la.xout = p.xf;
+    RS_CUDA(traced(T_LOCAL, double(n), s, [&] { return launch_local_sort(la, n > sk->tiny_max, pairs, 1u, s); }),
+            "launch local_sort (one array)");
+    return RS_OK;
+  }
   return run_lsd(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
                  static_cast<unsigned char*>(temp), false, ds, s);
 }

@@ -196,8 +196,9 @@ struct LocalArgs {
   const uint32_t* vin;
   uint32_t* vout;
   const uint64_t* seg_off;
-  const uint32_t* list;   // segment ids
+  const uint32_t* list;   // segment ids (null: one array of single_n keys)
   const uint32_t* count;  // device count of list entries
+  uint32_t single_n;      // keys of the one array when list is null (<= the block's tile)
   int num_digits;
   DigitSpec dig[kMaxDigits];
   KeyXform xin, xout;     // applied on loading kin, inverted on storing kout

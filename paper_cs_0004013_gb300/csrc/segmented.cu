@@ -238,11 +238,12 @@ __global__ void __launch_bounds__(THREADS, 1) local_sort_kernel(const LocalArgs 
   uint32_t* s_buf = reinterpret_cast<uint32_t*>(smem + L::OFF_BUF);
   uint32_t* s_warp = reinterpret_cast<uint32_t*>(smem + L::OFF_WARP);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t count = *a.count;
+  // a listed set of segments, or (list == null) the one array [0, single_n)
+  const uint32_t count = a.list ? *a.count : 1u;
   for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
-    const uint32_t s = a.list[k];
-    const uint64_t start = a.seg_off[s];
-    const uint32_t m = uint32_t(a.seg_off[s + 1] - start);
+    const uint32_t s = a.list ? a.list[k] : 0u;
+    const uint64_t start = a.list ? a.seg_off[s] : 0u;
+    const uint32_t m = a.list ? uint32_t(a.seg_off[s + 1] - start) : a.single_n;
     uint32_t key[ITEMS], val[PAIRS ? ITEMS : 1];
     const uint32_t wofs = uint32_t(warp) * 32 * ITEMS + lane;
 #pragma unroll
