@@ -223,7 +223,8 @@ rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p, in
   }
   const bool wide = needs_wide_status(n);
   uint32_t tile = (user && user->tile) ? user->tile : default_tile(p->R, pairs, n);
-  if (wide && !(user && user->tile)) tile = 1;  // only shape 0 has 64-bit status kernels
+  // 64-bit status kernels: shape 0 (keys and pairs) and shape 2 (keys)
+  if (wide && !(user && user->tile)) tile = (pairs || p->R != 8) ? 1u : 3u;
   rs_status st = pick_kernel(p->R, tile, vwords >= 0 ? vwords : (pairs ? 1 : 0), wide, &p->k);
   if (st != RS_OK) return st;
   p->num_tiles = (n + p->k->tile - 1) / p->k->tile;
