@@ -73,11 +73,11 @@ rs_status device_state(DeviceState** out) {
                 "cudaFuncSetAttribute(hist)");
     }
     const SegKernels* sk = seg_kernels();
-    const void* fn[7] = {sk->pass_keys,  sk->pass_pairs,  sk->tiny_keys, sk->tiny_pairs,
-                         sk->small_keys, sk->small_pairs, sk->hist};
-    const size_t sm[7] = {sk->pass_smem_keys,  sk->pass_smem_pairs,  sk->tiny_smem_keys, sk->tiny_smem_pairs,
-                          sk->small_smem_keys, sk->small_smem_pairs, sk->hist_smem};
-    for (int i = 0; i < 7; ++i)
+    const void* fn[8] = {sk->pass_keys,  sk->pass_pairs,  sk->tiny_keys, sk->tiny_pairs,
+                         sk->small_keys, sk->small_pairs, sk->hist,      sk->hist_xf};
+    const size_t sm[8] = {sk->pass_smem_keys,  sk->pass_smem_pairs,  sk->tiny_smem_keys, sk->tiny_smem_pairs,
+                          sk->small_smem_keys, sk->small_smem_pairs, sk->hist_smem,      sk->hist_smem};
+    for (int i = 0; i < 8; ++i)
       RS_CUDA(cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm[i])),
               "cudaFuncSetAttribute(segmented)");
     st.ready = true;
@@ -358,7 +358,7 @@ struct SegLayout {
 SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int nd, bool pairs) {
   const SegKernels* sk = seg_kernels();
   SegLayout L;
-  L.tiles_ub = size_t((total_n + sk->tile - 1) / sk->tile) + num_segs;
+  L.tiles_ub = size_t((total_n + sk->tile(pairs) - 1) / sk->tile(pairs)) + num_segs;
   off = align_up(off);
   L.counts = off;
   L.memset_from = off;
@@ -404,7 +404,7 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
                  num_segs,
                  sk->tiny_max,
                  sk->small_max,
-                 sk->tile,
+                 sk->tile(pairs),
                  reinterpret_cast<uint32_t*>(temp + L.large_seg),
                  reinterpret_cast<uint32_t*>(temp + L.tile_prefix),
                  reinterpret_cast<uint32_t*>(temp + L.small_seg),
@@ -419,7 +419,7 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
   ha.large_seg = pa.large_seg;
   ha.tile_prefix = pa.tile_prefix;
   ha.counts = counts;
-  ha.tile = sk->tile;
+  ha.tile = sk->tile(pairs);
   ha.num_digits = nd;
   for (int j = 0; j < nd; ++j) ha.dig[j] = dig[j];
   ha.seg_hist = reinterpret_cast<uint32_t*>(temp + L.seg_hist);

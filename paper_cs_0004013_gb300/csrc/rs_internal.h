@@ -205,7 +205,8 @@ struct LocalArgs {
 };
 
 struct SegKernels {
-  uint32_t tile, tiny_max, small_max;
+  uint32_t tile_keys, tile_pairs, tiny_max, small_max;
+  uint32_t tile(bool pairs) const { return pairs ? tile_pairs : tile_keys; }
   size_t pass_smem_keys, pass_smem_pairs, tiny_smem_keys, tiny_smem_pairs, small_smem_keys, small_smem_pairs;
   const void* pass_keys;
   const void* pass_pairs;
@@ -213,7 +214,8 @@ struct SegKernels {
   const void* tiny_pairs;
   const void* small_keys;
   const void* small_pairs;
-  const void* hist;
+  const void* hist;     // the segment histogram kernel for unsigned keys
+  const void* hist_xf;  // and for keys of another kind
   size_t hist_smem;
 };
 

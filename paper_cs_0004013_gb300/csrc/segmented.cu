@@ -89,7 +89,7 @@ __device__ __forceinline__ uint32_t find_segment(const uint32_t* tile_prefix, ui
 // digits); the copies are summed into the segment's global arrays when the
 // run moves on to the next segment, and at the end.  Also writes each
 // tile's job entry and clears its chained-scan status row.
-template <int THREADS>
+template <int THREADS, bool XF>
 __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs a) {
   extern __shared__ __align__(16) uint32_t sh[];  // [num_digits][256][32]
   const uint32_t num_large = a.counts[SEG_NUM_LARGE], total = a.counts[SEG_NUM_TILES];
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
     if (tid == 0)
       a.jobs[t] = SegTileJob{start, uint32_t(end - start), first, uint32_t(seg_start), uint32_t(seg_end), li, 0u};
     // eight loads in flight per thread before the counting (measured faster
-    // than two 16-byte vectors per thread)
+    // than two 16-byte vectors per thread, and than all of a tile's loads)
     for (uint64_t i0 = start + tid; i0 < end; i0 += 8 * THREADS) {
       uint32_t k[8];
 #pragma unroll
@@ -159,9 +159,10 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if (i0 + uint64_t(u) * THREADS >= end) break;
+        const uint32_t kk = XF ? to_ordered(k[u], xf) : k[u];
 #pragma unroll
         for (int j = 0; j < kMaxDigits; ++j)
-          if (j < nd) atomicAdd(&sh[(j * 256 + digit_of(to_ordered(k[u], xf), sft[j], wid[j])) * 32 + lane], 1u);
+          if (j < nd) atomicAdd(&sh[(j * 256 + digit_of(kk, sft[j], wid[j])) * 32 + lane], 1u);
       }
     }
     // this tile's chained-scan status row starts out "not ready"
@@ -323,7 +324,9 @@ cudaError_t launch_local(const LocalArgs& a, unsigned grid, cudaStream_t s) {
 }  // namespace
 
 // Tiled passes over large segments: 8-bit digits, 512 x 16 tiles.
-constexpr int kSegThreads = 512, kSegItems = 16;
+// Tiled passes over large segments: 512 x 24 tiles for keys, 512 x 16 with
+// payloads (the plain sort's best shapes).
+constexpr int kSegThreads = 512, kSegItemsKeys = 24, kSegItemsPairs = 16;
 // Local sorts: tiny segments <= 256 x 16 keys, small ones <= 1024 x 16 keys.
 constexpr int kTinyThreads = 256, kSmallThreads = 1024, kLocalItems = 16;
 // Segment histograms: one 1024-thread block per SM (lane copies of up to
@@ -332,22 +335,24 @@ constexpr int kSegHistThreads = 1024;
 
 const SegKernels* seg_kernels() {
   static const SegKernels k = {
-      uint32_t(kSegThreads * kSegItems),
+      uint32_t(kSegThreads * kSegItemsKeys),
+      uint32_t(kSegThreads * kSegItemsPairs),
       uint32_t(kTinyThreads * kLocalItems),
       uint32_t(kSmallThreads * kLocalItems),
-      OnesweepLayout<8, kSegThreads, kSegItems, false>::SMEM,
-      OnesweepLayout<8, kSegThreads, kSegItems, true>::SMEM,
+      OnesweepLayout<8, kSegThreads, kSegItemsKeys, 0>::SMEM,
+      OnesweepLayout<8, kSegThreads, kSegItemsPairs, 1>::SMEM,
       LocalLayout<kTinyThreads, kLocalItems, false>::SMEM,
       LocalLayout<kTinyThreads, kLocalItems, true>::SMEM,
       LocalLayout<kSmallThreads, kLocalItems, false>::SMEM,
       LocalLayout<kSmallThreads, kLocalItems, true>::SMEM,
-      reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItems, false, 2>),
-      reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItems, true, 2>),
+      reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsKeys, false, 2>),
+      reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsPairs, true, 2>),
       reinterpret_cast<const void*>(&local_sort_kernel<kTinyThreads, kLocalItems, false>),
       reinterpret_cast<const void*>(&local_sort_kernel<kTinyThreads, kLocalItems, true>),
       reinterpret_cast<const void*>(&local_sort_kernel<kSmallThreads, kLocalItems, false>),
       reinterpret_cast<const void*>(&local_sort_kernel<kSmallThreads, kLocalItems, true>),
-      reinterpret_cast<const void*>(&seg_hist_kernel<kSegHistThreads>),
+      reinterpret_cast<const void*>(&seg_hist_kernel<kSegHistThreads, false>),
+      reinterpret_cast<const void*>(&seg_hist_kernel<kSegHistThreads, true>),
       size_t(kMaxDigits) * 256 * 32 * 4,
   };
   return &k;
@@ -358,7 +363,9 @@ cudaError_t launch_seg_plan(const SegPlanArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_seg_hist(const SegHistArgs& a, unsigned grid, cudaStream_t s) {
-  seg_hist_kernel<kSegHistThreads><<<grid, kSegHistThreads, size_t(a.num_digits) * 256 * 32 * 4, s>>>(a);
+  const size_t smem = size_t(a.num_digits) * 256 * 32 * 4;
+  if (is_identity(a.xform)) seg_hist_kernel<kSegHistThreads, false><<<grid, kSegHistThreads, smem, s>>>(a);
+  else seg_hist_kernel<kSegHistThreads, true><<<grid, kSegHistThreads, smem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_seg_scan(const SegScanArgs& a, unsigned grid, cudaStream_t s) {
@@ -366,8 +373,8 @@ cudaError_t launch_seg_scan(const SegScanArgs& a, unsigned grid, cudaStream_t s)
   return cudaGetLastError();
 }
 cudaError_t launch_seg_pass(const SegPassArgs& a, bool pairs, unsigned grid, cudaStream_t s) {
-  return pairs ? launch_seg_pass<kSegThreads, kSegItems, true, 2>(a, grid, s)
-               : launch_seg_pass<kSegThreads, kSegItems, false, 2>(a, grid, s);
+  return pairs ? launch_seg_pass<kSegThreads, kSegItemsPairs, true, 2>(a, grid, s)
+               : launch_seg_pass<kSegThreads, kSegItemsKeys, false, 2>(a, grid, s);
 }
 cudaError_t launch_local_sort(const LocalArgs& a, bool small, bool pairs, unsigned grid, cudaStream_t s) {
   if (small)
