@@ -117,7 +117,7 @@ class SortServer:
     batch arena in keys; direct_min_keys: requests this large are sorted on
     their own, from and into their pinned buffers."""
 
-    def __init__(self, slots: int = 4, streams: int = 4, mem_budget: int = 8 << 30,
+    def __init__(self, slots: int = 8, streams: int = 8, mem_budget: int = 8 << 30,
                  max_batch_keys: int = 1 << 24, num_parts: int = 64, device: str = "cuda",
                  direct_min_keys: int = 1 << 22):
         import torch
