@@ -144,6 +144,17 @@ rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in,
                         uint32_t shift, uint32_t width, void* temp,
                         size_t* temp_bytes, rs_stream_t stream);
 
+/* rs_sort_u32_pairs with 64-bit values (vals_in, vals_out: DEVICE, n uint64
+ * each, 8-byte aligned): stable by key.  The values are split into planes of
+ * low and high 32-bit words, both carried by every pass (the kernel moves
+ * two payload words per key) and joined again at the end.  plan: LSD with
+ * 8-bit digits (0 fields are fine); key_kind as for the other sorts.       */
+rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in,
+                              uint32_t* keys_out, uint64_t* vals_out, uint64_t n,
+                              uint32_t num_parts, uint64_t* h_part_offsets,
+                              const rs_plan* plan, void* temp, size_t* temp_bytes,
+                              rs_stream_t stream);
+
 /* ---- 64-bit keys ------------------------------------------------------- */
 
 /* Sort n 64-bit keys ascending (keys_in, keys_out: DEVICE, n uint64 each,

@@ -120,7 +120,9 @@ def sort_pairs(keys, vals, kind: str = "u32") -> tuple[np.ndarray, np.ndarray]:
     """(key, value) pairs ordered by key alone; equal keys keep input order
     (Sec. 3.3.1, Sec. 5)."""
     keys = _words(keys, kind)
-    vals = _u32(vals)
+    vals = np.asarray(vals)
+    if vals.dtype != np.uint64:  # payloads of 32 bits, or 64 bits carried as they are
+        vals = _u32(vals)
     if keys.shape != vals.shape:
         raise ValueError("keys and vals differ in length")
     perm = order_perm(keys, kind)

@@ -288,9 +288,12 @@ void part_offsets_host(uint64_t n, uint32_t parts, uint64_t* out) {
 // ---- the LSD pipeline ---------------------------------------------------------
 // memset(ctrl + hist) -> upfront histogram (+ clear status) -> digit scans ->
 // one onesweep pass per digit.
+// vals2_*: a second payload word per key (kernels with two payload words),
+// its input, output and alternate planes; null for one word or none.
 rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, const uint32_t* vals_in,
                   uint32_t* keys_out, uint32_t* vals_out, uint32_t n, unsigned char* temp, bool force_all,
-                  DeviceState* ds, cudaStream_t s) {
+                  DeviceState* ds, cudaStream_t s, const uint32_t* vals2_in = nullptr, uint32_t* vals2_out = nullptr,
+                  uint32_t* vals2_alt = nullptr) {
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + L.ctrl);
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp + L.hist);
   uint32_t* bases = reinterpret_cast<uint32_t*>(temp + L.bases);
@@ -325,6 +328,9 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
     pa.vals_in = vals_in;
     pa.vals_out = vals_out;
     pa.vals_alt = L.alt_v ? reinterpret_cast<uint32_t*>(temp + L.alt_v) : vals_out;
+    pa.vals2_in = vals2_in;
+    pa.vals2_out = vals2_out;
+    pa.vals2_alt = vals2_alt;
     pa.n = n;
     pa.shift = p.dig[j].shift;
     pa.width = p.dig[j].width;
@@ -883,6 +889,67 @@ rs_status rs_sort_u64_pairs(const uint64_t* keys_in, const uint32_t* vals_in, ui
                             const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
   return sort64_impl(keys_in, vals_in, keys_out, vals_out, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
                      stream, true);
+}
+
+rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in, uint32_t* keys_out,
+                              uint64_t* vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
+                              const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
+  g_last_error.clear();
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  rs_status st = check_common(keys_in, keys_out, n, temp, temp_bytes);
+  if (st != RS_OK) return st;
+  if (num_parts < 1) return fail(RS_ERR_INVALID, "num_parts must be >= 1");
+  if (plan && plan->mode == RS_MODE_MSD) return fail(RS_ERR_UNSUPPORTED, "64-bit values use the LSD plan");
+  if (plan && plan->digit_bits && plan->digit_bits != 8) return fail(RS_ERR_UNSUPPORTED, "64-bit values use 8-bit digits");
+  rs_plan q = plan ? *plan : rs_plan{0, 0, 0, 0};
+  q.digit_bits = 8;
+  q.mode = RS_MODE_LSD;
+  SortPlan p;
+  if ((st = make_plan(n, true, &q, &p, 2)) != RS_OK) return st;
+  // the sort's own layout (keys, the low value words as the first payload
+  // plane) followed by the value planes: low and high words of the input and
+  // the output, and the high words' alternate plane
+  Layout L = make_layout(p, n, true);
+  size_t plane[5];
+  size_t off = L.total;
+  for (int i = 0; i < 5; ++i) {
+    plane[i] = off;
+    off = align_up(off + size_t(n) * 4);
+  }
+  const size_t need = off;
+  if (!temp) {
+    *temp_bytes = need;
+    return RS_OK;
+  }
+  if (*temp_bytes < need) return fail(RS_ERR_TEMP_TOO_SMALL, "temp_bytes = %zu, need %zu", *temp_bytes, need);
+  const size_t kb = size_t(n) * 4, vb = size_t(n) * 8;
+  if (n > 0) {
+    if (!vals_in || !vals_out) return fail(RS_ERR_INVALID, "NULL value buffer");
+    if ((reinterpret_cast<uintptr_t>(vals_in) | reinterpret_cast<uintptr_t>(vals_out)) & 7)
+      return fail(RS_ERR_INVALID, "64-bit value buffers must be 8-byte aligned");
+    if (overlaps(keys_out, kb, keys_in, kb) || overlaps(keys_out, kb, vals_in, vb) ||
+        overlaps(vals_out, vb, keys_in, kb) || overlaps(vals_out, vb, vals_in, vb) ||
+        overlaps(vals_out, vb, keys_out, kb) || overlaps(keys_out, kb, temp, need) ||
+        overlaps(vals_out, vb, temp, need) || overlaps(keys_in, kb, temp, need) || overlaps(vals_in, vb, temp, need))
+      return fail(RS_ERR_INVALID, "a buffer overlaps another");
+  }
+  if (h_part_offsets) part_offsets_host(n, num_parts, h_part_offsets);
+  if (n == 0) return RS_OK;
+  DeviceState* ds = nullptr;
+  if ((st = device_state(&ds)) != RS_OK) return st;
+  unsigned char* t = static_cast<unsigned char*>(temp);
+  uint32_t* pl[5];
+  for (int i = 0; i < 5; ++i) pl[i] = reinterpret_cast<uint32_t*>(t + plane[i]);
+  uint32_t *vlo_in = pl[0], *vhi_in = pl[1], *vlo_out = pl[2], *vhi_out = pl[3], *vhi_alt = pl[4];
+  const unsigned egrid = unsigned(std::min<size_t>((size_t(n) + 255) / 256, size_t(ds->num_sms) * 8));
+  const KeyXform64 ident{0u, 0u, 0u};
+  WideArgs wa{reinterpret_cast<const uint2*>(vals_in), nullptr, vlo_in, vhi_in, n, ident};
+  RS_CUDA(traced(T_SPLIT, double(n), s, [&] { return launch_split64(wa, egrid, s); }), "launch split64 (values)");
+  st = run_lsd(p, L, keys_in, vlo_in, keys_out, vlo_out, uint32_t(n), t, false, ds, s, vhi_in, vhi_out, vhi_alt);
+  if (st != RS_OK) return st;
+  WideArgs ja{nullptr, reinterpret_cast<uint2*>(vals_out), vlo_out, vhi_out, n, ident};
+  RS_CUDA(traced(T_JOIN, double(n), s, [&] { return launch_join64(ja, egrid, s); }), "launch join64 (values)");
+  return RS_OK;
 }
 
 rs_status rs_merge_u32(const uint32_t* a, const uint32_t* va, uint64_t na, const uint32_t* b, const uint32_t* vb,

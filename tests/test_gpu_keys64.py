@@ -111,3 +111,22 @@ def test_pairs_stable_and_skipped(rs, kind):
     _check_pairs(rs, r % np.uint64(97) * np.uint64(0x0101010101010101), kind)  # few distinct keys
     _check_pairs(rs, r & np.uint64(0xFFFF00000000), kind)                    # six digits constant
     _check_pairs(rs, np.full(n, 0xC000000000000000, np.uint64), kind)        # every digit skipped
+
+
+@pytest.mark.parametrize("kind", ["u32", "i32", "f32"])
+@pytest.mark.parametrize("n", [1, 1000, 3 * TILE + 5, 1 << 20])
+def test_u32_keys_u64_values(rs, kind, n):
+    """32-bit keys carrying 64-bit values (rs_sort_u32_pairs64): stable."""
+    import torch
+    keys = synth.splitmix64(90 + n, (n + 1) // 2).view(np.uint32)[:n].copy()
+    keys[::3] = keys[0]  # many equal keys
+    vals = synth.splitmix64(91 + n, n) ^ np.arange(n, dtype=np.uint64)
+    dk = torch.from_numpy(keys.view(np.int32).copy()).cuda()
+    dv = torch.from_numpy(vals.view(np.int64).copy()).cuda()
+    ko, vo, offs = rs.sort_pairs64(dk, dv, plan={"key_kind": {"u32": 0, "i32": 1, "f32": 2}[kind]})
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk, wv = oracle.sort_pairs(keys, vals, kind)
+    assert np.array_equal(ko.cpu().numpy().view(np.uint32), wk)
+    assert np.array_equal(vo.cpu().numpy().view(np.uint64), wv)
+    assert np.array_equal(offs, oracle.partition_offsets(n, 64))
