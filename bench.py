@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--pairs", action="store_true", help="time key+payload sorts as the main value")
     ap.add_argument("--keys64", action="store_true", help="64-bit keys (rs_sort_u64), uniform over all 2^64 words")
+    ap.add_argument("--vals64", action="store_true",
+                    help="32-bit keys with 64-bit values (rs_sort_u32_pairs64) as the main value")
     ap.add_argument("--key-kind", choices=["u32", "i32", "f32"], default="u32",
                     help="how the 32-bit key words are ordered (u32: the headline workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -272,8 +274,14 @@ def run_ours(args):
         d_keys = torch.from_numpy(keys.view(np.int32)).to(dev)
     d_out = torch.empty_like(d_keys)
     plan = {"digit_bits": args.digit_bits, "tile": args.tile, "key_kind": KEY_KINDS[args.key_kind]}
-    pairs = args.pairs
-    if wide:
+    vals64 = args.vals64 and not wide
+    pairs = args.pairs or vals64
+    if vals64:
+        d_vals = torch.arange(n, dtype=torch.int64, device=dev)
+        d_vout = torch.empty_like(d_vals)
+        temp = torch.empty(rs.rs_sort_u32_pairs64(None, None, None, None, n, plan=plan), dtype=torch.uint8,
+                           device=dev)
+    elif wide:
         if pairs:
             d_vals = torch.arange(n, dtype=torch.int32, device=dev)
             d_vout = torch.empty_like(d_vals)
@@ -291,7 +299,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        if wide and pairs:
+        if vals64:
+            rs.rs_sort_u32_pairs64(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
+        elif wide and pairs:
             rs.rs_sort_u64_pairs(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
         elif wide:
             rs.rs_sort_u64(d_keys, d_out, n, 64, plan, temp, stream, want_offsets=True)
@@ -318,7 +328,7 @@ def run_ours(args):
     # weigh on small sorts
     # inputs that fit in L2 are evicted before every timed step (a write of
     # a buffer larger than L2), and each step is timed on its own
-    flush_l2 = 4 * n * (2 if pairs else 1) * 2 < L2_BYTES
+    flush_l2 = 4 * n * (3 if vals64 else 2 if pairs else 1) * 2 < L2_BYTES
     flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev) if flush_l2 else None
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
@@ -358,10 +368,16 @@ def run_ours(args):
             pass_kind = k
     passes = trace[pass_kind]["launches"] // args.steps if pass_kind else 0
     # per key and pass: read + write of the words moved
-    word_bytes = 8 * ((2 if wide else 1) + (1 if pairs else 0))
-    # 64-bit keys add the split and the join (8 B read + 8 B written each) and
-    # histogram both word planes
-    bpk = (32 + 8 if wide else 4) + passes * word_bytes
+    word_bytes = 8 * ((2 if wide else 1) + (2 if vals64 else 1 if pairs else 0))
+    # 64-bit keys: the histograms read the interleaved keys twice (one launch
+    # per word); where the words are split into planes first, the split and
+    # the join (8 B read + 8 B written each) replace that by a read of each
+    # plane.  64-bit values that are split and joined add the same 32 B.
+    split = "split64" in trace
+    if wide:
+        bpk = (32 + 8 if split else 16) + passes * word_bytes
+    else:
+        bpk = (32 if split else 0) + 4 + passes * word_bytes
     peak, peak_kind = measured_peak()
     roof = None
     if pass_kind:
@@ -369,7 +385,7 @@ def run_ours(args):
         avg_ms = tr["total_ms"] / tr["launches"]
         bytes_launch = word_bytes * tr["keys"] / tr["launches"]
         achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
-        key = f"{pass_kind}_{'keys64' if wide else ('pairs' if pairs else 'keys')}_n{n}"
+        key = f"{pass_kind}_{'keys64' if wide else ('pairs64' if vals64 else 'pairs' if pairs else 'keys')}_n{n}"
         traffic = traffic_from_profiles("onesweep.cuh", key)
         roof = {"bound": "hbm", "kernel": pass_kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -395,7 +411,7 @@ def run_ours(args):
     # (the host link carries both directions at once).  The one-stream figure
     # (copy in, sort, copy out, strictly one after another) is reported beside.
     e2e = None
-    if not args.no_e2e and not wide:
+    if not args.no_e2e and not wide and not vals64:
         h_in = torch.from_numpy(keys.view(np.int32)).pin_memory()
         h_vin = torch.arange(n, dtype=torch.int32).pin_memory() if pairs else None
         nb = rs.rs_sort_u32_host(None, h_vin, None, h_vin, n, plan=plan)
@@ -451,7 +467,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "Gkeys/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64" if wide else "u32", "data": "synthetic",
-            "config": {"workload": (workload_label(n, pairs, args.key_kind) if not wide else
+            "config": {"workload": (workload_label(n, pairs, args.key_kind).replace("key+payload", "key+64-bit value")
+                                    if vals64 else workload_label(n, pairs, args.key_kind) if not wide else
                                     workload_label(n, pairs).replace("uint32 keys uniform in [0, 2^31-1]",
                                                                      "uint64 keys uniform over all 2^64 values")),
                        "n": n, "digit_bits": args.digit_bits or "auto", "passes": passes,

@@ -145,10 +145,11 @@ rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in,
                         size_t* temp_bytes, rs_stream_t stream);
 
 /* rs_sort_u32_pairs with 64-bit values (vals_in, vals_out: DEVICE, n uint64
- * each, 8-byte aligned): stable by key.  The values are split into planes of
- * low and high 32-bit words, both carried by every pass (the kernel moves
- * two payload words per key) and joined again at the end.  plan: LSD with
- * 8-bit digits (0 fields are fine); key_kind as for the other sorts.       */
+ * each, 8-byte aligned): stable by key.  Every pass carries the value's low
+ * and high 32-bit words as two payload words per key (word planes in temp
+ * between passes); the first pass reads the interleaved values and the last
+ * writes them.  plan: LSD with 8-bit digits (0 fields are fine); key_kind as
+ * for the other sorts.  Temp: the key+payload temp plus three n-word planes. */
 rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in,
                               uint32_t* keys_out, uint64_t* vals_out, uint64_t n,
                               uint32_t num_parts, uint64_t* h_part_offsets,
@@ -161,13 +162,14 @@ rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in,
  * 8-byte aligned, not overlapping) and write the partition offsets as for
  * rs_sort_u32.  No counterpart in the paper, whose keys are 32-bit (Sec. 1.1);
  * the method is the same LSD radix distribution (Sec. 3.3.1) with eight
- * 8-bit digits.  The keys are split into planes of low and high 32-bit
- * words; each pass moves both words, the low word serving as the key for
- * digits 0-3 and the high word for digits 4-7.  plan: digit_bits must be 0
+ * 8-bit digits.  Between passes the keys are held as planes of low and
+ * high 32-bit words; each pass moves both words, the low word serving as the
+ * key for digits 0-3 and the high word for digits 4-7.  plan: digit_bits must be 0
  * or 8, mode LSD (or 0), tile selects the key+payload tile shape, and
  * key_kind orders the 64-bit words as unsigned (RS_KEY_U32), two's-complement
  * signed (RS_KEY_I32) or IEEE-754 binary64 totalOrder (RS_KEY_F32).  Temp:
- * six n-word planes plus histograms and status.                             */
+ * four n-word planes (six with the persistent tile shapes, which split the
+ * keys into planes first) plus histograms and status.                       */
 rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n,
                       uint32_t num_parts, uint64_t* h_part_offsets,
                       const rs_plan* plan, void* temp, size_t* temp_bytes,

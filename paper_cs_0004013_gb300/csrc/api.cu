@@ -68,9 +68,10 @@ rs_status device_state(DeviceState** out) {
         RS_CUDA(cudaFuncSetAttribute(ks[i].func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks[i].smem)),
                 "cudaFuncSetAttribute(onesweep)");
       const HistKernel* h = hist_kernel(r);
-      for (const void* f : {h->func, h->func_xf})
-        RS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
-                "cudaFuncSetAttribute(hist)");
+      for (const void* f : {h->func, h->func_xf, h->func_w64})
+        if (f)
+          RS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
+                  "cudaFuncSetAttribute(hist)");
     }
     const SegKernels* sk = seg_kernels();
     const void* fn[8] = {sk->pass_keys,  sk->pass_pairs,  sk->tiny_keys, sk->tiny_pairs,
@@ -293,7 +294,7 @@ void part_offsets_host(uint64_t n, uint32_t parts, uint64_t* out) {
 rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, const uint32_t* vals_in,
                   uint32_t* keys_out, uint32_t* vals_out, uint32_t n, unsigned char* temp, bool force_all,
                   DeviceState* ds, cudaStream_t s, const uint32_t* vals2_in = nullptr, uint32_t* vals2_out = nullptr,
-                  uint32_t* vals2_alt = nullptr) {
+                  uint32_t* vals2_alt = nullptr, const uint2* pair_vals_in = nullptr, uint2* pair_vals_out = nullptr) {
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + L.ctrl);
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp + L.hist);
   uint32_t* bases = reinterpret_cast<uint32_t*>(temp + L.bases);
@@ -343,6 +344,8 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
     pa.err = ds->err;
     pa.xin = p.xf;   // the first executed pass maps the input keys
     pa.xout = p.xf;  // the last one maps them back
+    pa.pair_in = pair_vals_in;  // 64-bit values read and written interleaved
+    pa.pair_out = pair_vals_out;
     RS_CUDA(traced(p.R == 8 ? T_PASS8 : T_PASS11, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }),
             "launch onesweep");
   }
@@ -669,19 +672,25 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
 
 // ---- 64-bit keys -----------------------------------------------------------------
 // Eight 8-bit digits; the key+payload pass kernel moves both words of every
-// key (low word as the key for digits 0-3, high word for digits 4-7).
+// key (low word as the key for digits 0-3, high word for digits 4-7).  With a
+// tiled (non-persistent) pass kernel the histograms and the first executed
+// pass read the interleaved keys and the last one writes them (fused); the
+// persistent kernels take word planes made by a split kernel and joined back
+// at the end.
 struct Layout64 {
+  bool fused = false;
   size_t ctrl = 0;    // [0, 8): tile tickets of the 8 passes; [8, 16): skip flags
   size_t hist = 0;    // [8][256]
   size_t bases = 0;   // [8][256]
   size_t status = 0, status_bytes = 0;
-  size_t plane[6] = {};  // lo/hi words of the input, output and alternate order
+  size_t plane[6] = {};  // lo/hi words of the output, alternate and (split only) input order
   size_t val_alt = 0;    // the values' alternate plane (key+value sorts)
   size_t memset_bytes = 0, total = 0;
 };
 
 Layout64 make_layout64(const SortPlan& p, uint64_t n, bool pairs) {
   Layout64 L;
+  L.fused = p.k->persistent_per_sm == 0;
   size_t off = 0;
   L.ctrl = off;
   off += kAlign;
@@ -693,7 +702,7 @@ Layout64 make_layout64(const SortPlan& p, uint64_t n, bool pairs) {
   L.status = off;
   L.status_bytes = p.num_tiles * 256 * (p.k->wide_status ? 8 : 4);
   off = align_up(off + L.status_bytes);
-  for (int i = 0; i < 6; ++i) {
+  for (int i = 0; i < (L.fused ? 4 : 6); ++i) {
     L.plane[i] = off;
     off = align_up(off + size_t(n) * 4);
   }
@@ -721,22 +730,31 @@ rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_i
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + L.ctrl);
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp + L.hist);
   uint32_t* bases = reinterpret_cast<uint32_t*>(temp + L.bases);
-  uint32_t* pl[6];
-  for (int i = 0; i < 6; ++i) pl[i] = reinterpret_cast<uint32_t*>(temp + L.plane[i]);
-  uint32_t *lo_in = pl[0], *hi_in = pl[1], *lo_out = pl[2], *hi_out = pl[3], *lo_alt = pl[4], *hi_alt = pl[5];
+  uint32_t* pl[6] = {};
+  for (int i = 0; i < (L.fused ? 4 : 6); ++i) pl[i] = reinterpret_cast<uint32_t*>(temp + L.plane[i]);
+  uint32_t *lo_out = pl[0], *hi_out = pl[1], *lo_alt = pl[2], *hi_alt = pl[3], *lo_in = pl[4], *hi_in = pl[5];
+  const uint2* k2 = reinterpret_cast<const uint2*>(keys_in);
   RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, L.memset_bytes, s); }),
           "cudaMemsetAsync(temp)");
   const unsigned egrid = unsigned(std::min<size_t>((size_t(n) + 255) / 256, size_t(ds->num_sms) * 8));
-  WideArgs wa{reinterpret_cast<const uint2*>(keys_in), reinterpret_cast<uint2*>(keys_out), lo_in, hi_in, n, x};
-  RS_CUDA(traced(T_SPLIT, n, s, [&] { return launch_split64(wa, egrid, s); }), "launch split64");
-  // the eight digit histograms: four per word plane
+  if (!L.fused) {
+    WideArgs wa{k2, reinterpret_cast<uint2*>(keys_out), lo_in, hi_in, n, x};
+    RS_CUDA(traced(T_SPLIT, n, s, [&] { return launch_split64(wa, egrid, s); }), "launch split64");
+  }
+  // the eight digit histograms: four per word
   const HistKernel* hk = hist_kernel(8);
   const size_t work = (size_t(n) + 4095) / 4096;
   unsigned hgrid = unsigned(ds->num_sms);
   if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
   for (int w = 0; w < 2; ++w) {
     HistArgs ha{};
-    ha.keys = w == 0 ? lo_in : hi_in;
+    if (L.fused) {
+      ha.keys64 = k2;
+      ha.word64 = uint32_t(w);
+      ha.x64 = x;
+    } else {
+      ha.keys = w == 0 ? lo_in : hi_in;
+    }
     ha.n = n;
     ha.num_digits = 4;
     for (int j = 0; j < 4; ++j) ha.dig[j] = DigitSpec{uint32_t(8 * j), 8u};
@@ -771,13 +789,21 @@ rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_i
     pa.status = temp + L.status;
     pa.tile_counter = ctrl + j;
     pa.err = ds->err;
-    pa.xin = kIdentityXform;   // the planes already hold mapped words
+    pa.xin = kIdentityXform;   // the planes hold mapped words
     pa.xout = kIdentityXform;
+    if (L.fused) {  // the first executed pass reads the keys, the last one writes them
+      pa.pair_in = k2;
+      pa.pair_out = reinterpret_cast<uint2*>(keys_out);
+      pa.pair_key = 1;
+      pa.key_high = high ? 1u : 0u;
+      pa.x64 = x;
+    }
     RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }), "launch onesweep (64-bit)");
   }
-  // the last executed pass always writes the output planes
-  WideArgs ja{nullptr, reinterpret_cast<uint2*>(keys_out), lo_out, hi_out, n, x};
-  RS_CUDA(traced(T_JOIN, n, s, [&] { return launch_join64(ja, egrid, s); }), "launch join64");
+  if (!L.fused) {  // the last executed pass always writes the output planes
+    WideArgs ja{nullptr, reinterpret_cast<uint2*>(keys_out), lo_out, hi_out, n, x};
+    RS_CUDA(traced(T_JOIN, n, s, [&] { return launch_join64(ja, egrid, s); }), "launch join64");
+  }
   return RS_OK;
 }
 
@@ -907,12 +933,16 @@ rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in, 
   SortPlan p;
   if ((st = make_plan(n, true, &q, &p, 2)) != RS_OK) return st;
   // the sort's own layout (keys, the low value words as the first payload
-  // plane) followed by the value planes: low and high words of the input and
-  // the output, and the high words' alternate plane
+  // plane) followed by the value planes: low and high words of the output,
+  // the high words' alternate plane and (split only) both words of the input.
+  // A tiled pass kernel reads and writes the interleaved values itself
+  // (fused); a persistent one takes planes split and joined by kernels.
   Layout L = make_layout(p, n, true);
-  size_t plane[5];
+  const bool fused = p.k->persistent_per_sm == 0;
+  const int nplanes = fused ? 3 : 5;
+  size_t plane[5] = {};
   size_t off = L.total;
-  for (int i = 0; i < 5; ++i) {
+  for (int i = 0; i < nplanes; ++i) {
     plane[i] = off;
     off = align_up(off + size_t(n) * 4);
   }
@@ -938,9 +968,12 @@ rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in, 
   DeviceState* ds = nullptr;
   if ((st = device_state(&ds)) != RS_OK) return st;
   unsigned char* t = static_cast<unsigned char*>(temp);
-  uint32_t* pl[5];
-  for (int i = 0; i < 5; ++i) pl[i] = reinterpret_cast<uint32_t*>(t + plane[i]);
-  uint32_t *vlo_in = pl[0], *vhi_in = pl[1], *vlo_out = pl[2], *vhi_out = pl[3], *vhi_alt = pl[4];
+  uint32_t* pl[5] = {};
+  for (int i = 0; i < nplanes; ++i) pl[i] = reinterpret_cast<uint32_t*>(t + plane[i]);
+  uint32_t *vlo_out = pl[0], *vhi_out = pl[1], *vhi_alt = pl[2], *vlo_in = pl[3], *vhi_in = pl[4];
+  if (fused)
+    return run_lsd(p, L, keys_in, nullptr, keys_out, vlo_out, uint32_t(n), t, false, ds, s, nullptr, vhi_out,
+                   vhi_alt, reinterpret_cast<const uint2*>(vals_in), reinterpret_cast<uint2*>(vals_out));
   const unsigned egrid = unsigned(std::min<size_t>((size_t(n) + 255) / 256, size_t(ds->num_sms) * 8));
   const KeyXform64 ident{0u, 0u, 0u};
   WideArgs wa{reinterpret_cast<const uint2*>(vals_in), nullptr, vlo_in, vhi_in, n, ident};

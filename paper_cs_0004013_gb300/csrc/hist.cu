@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(THREADS) upfront_hist_kernel(const HistArgs a)
 // every key has the same digit), so the kernel runs at the speed of its
 // loads.  Copies of one warp-lane position are shared by the block's warps
 // (atomics still needed), 128 KiB of shared memory for four digits.
-template <int THREADS, bool XF>
+// W64: the keys are interleaved 64-bit words; the digits come from one word
+// of their order map (two launches cover the eight digits).
+template <int THREADS, bool XF, bool W64>
 __global__ void __launch_bounds__(THREADS, 1) upfront_hist_lanes_kernel(const HistArgs a) {
   constexpr int BINS = 256;
   extern __shared__ __align__(16) uint32_t sh[];  // [num_digits][256][32]
@@ -110,31 +112,64 @@ __global__ void __launch_bounds__(THREADS, 1) upfront_hist_lanes_kernel(const Hi
       if (j < nd) atomicAdd(&sh[(j * BINS + digit_of(k, sft[j], wid[j])) * 32 + lane], 1u);
   };
   const uint32_t n = a.n;
-  const uint32_t mis = uint32_t((reinterpret_cast<uintptr_t>(a.keys) >> 2) & 3u);
-  uint32_t head = (4u - mis) & 3u;
-  if (head > n) head = n;
-  const size_t nvec = size_t(n - head) / 4;
-  const uint32_t tail = head + uint32_t(nvec * 4);
-  if (blockIdx.x == gridDim.x - 1) {
-    for (uint32_t i = tid; i < head; i += THREADS) count(a.keys[i]);
-    for (uint32_t i = tail + tid; i < n; i += THREADS) count(a.keys[i]);
-  }
-  const uint4* v4 = reinterpret_cast<const uint4*>(a.keys + head);
   const size_t stride = size_t(gridDim.x) * THREADS;
-  size_t i = size_t(blockIdx.x) * THREADS + tid;
-  for (; i + 3 * stride < nvec; i += 4 * stride) {
-    const uint4 x0 = ld_stream4(v4 + i);
-    const uint4 x1 = ld_stream4(v4 + i + stride);
-    const uint4 x2 = ld_stream4(v4 + i + 2 * stride);
-    const uint4 x3 = ld_stream4(v4 + i + 3 * stride);
-    count(x0.x); count(x0.y); count(x0.z); count(x0.w);
-    count(x1.x); count(x1.y); count(x1.z); count(x1.w);
-    count(x2.x); count(x2.y); count(x2.z); count(x2.w);
-    count(x3.x); count(x3.y); count(x3.z); count(x3.w);
-  }
-  for (; i < nvec; i += stride) {
-    const uint4 x = ld_stream4(v4 + i);
-    count(x.x); count(x.y); count(x.z); count(x.w);
+  if constexpr (W64) {
+    const KeyXform64 x64 = a.x64;
+    const bool hi = a.word64 != 0;
+    auto count64 = [&](uint32_t lo, uint32_t hw) {
+      const uint2 m = map64(make_uint2(lo, hw), x64);
+      count(hi ? m.y : m.x);
+    };
+    // one key before the first 16-byte boundary, one after the last pair
+    const uint32_t head = ((reinterpret_cast<uintptr_t>(a.keys64) >> 3) & 1u) && n > 0 ? 1u : 0u;
+    const size_t nvec = size_t(n - head) / 2;
+    const uint32_t tail = head + uint32_t(nvec * 2);
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) {
+      if (head) count64(a.keys64[0].x, a.keys64[0].y);
+      if (tail < n) count64(a.keys64[tail].x, a.keys64[tail].y);
+    }
+    const uint4* v4 = reinterpret_cast<const uint4*>(a.keys64 + head);
+    size_t i = size_t(blockIdx.x) * THREADS + tid;
+    for (; i + 3 * stride < nvec; i += 4 * stride) {
+      const uint4 x0 = ld_stream4(v4 + i);
+      const uint4 x1 = ld_stream4(v4 + i + stride);
+      const uint4 x2 = ld_stream4(v4 + i + 2 * stride);
+      const uint4 x3 = ld_stream4(v4 + i + 3 * stride);
+      count64(x0.x, x0.y); count64(x0.z, x0.w);
+      count64(x1.x, x1.y); count64(x1.z, x1.w);
+      count64(x2.x, x2.y); count64(x2.z, x2.w);
+      count64(x3.x, x3.y); count64(x3.z, x3.w);
+    }
+    for (; i < nvec; i += stride) {
+      const uint4 x = ld_stream4(v4 + i);
+      count64(x.x, x.y); count64(x.z, x.w);
+    }
+  } else {
+    const uint32_t mis = uint32_t((reinterpret_cast<uintptr_t>(a.keys) >> 2) & 3u);
+    uint32_t head = (4u - mis) & 3u;
+    if (head > n) head = n;
+    const size_t nvec = size_t(n - head) / 4;
+    const uint32_t tail = head + uint32_t(nvec * 4);
+    if (blockIdx.x == gridDim.x - 1) {
+      for (uint32_t i = tid; i < head; i += THREADS) count(a.keys[i]);
+      for (uint32_t i = tail + tid; i < n; i += THREADS) count(a.keys[i]);
+    }
+    const uint4* v4 = reinterpret_cast<const uint4*>(a.keys + head);
+    size_t i = size_t(blockIdx.x) * THREADS + tid;
+    for (; i + 3 * stride < nvec; i += 4 * stride) {
+      const uint4 x0 = ld_stream4(v4 + i);
+      const uint4 x1 = ld_stream4(v4 + i + stride);
+      const uint4 x2 = ld_stream4(v4 + i + 2 * stride);
+      const uint4 x3 = ld_stream4(v4 + i + 3 * stride);
+      count(x0.x); count(x0.y); count(x0.z); count(x0.w);
+      count(x1.x); count(x1.y); count(x1.z); count(x1.w);
+      count(x2.x); count(x2.y); count(x2.z); count(x2.w);
+      count(x3.x); count(x3.y); count(x3.z); count(x3.w);
+    }
+    for (; i < nvec; i += stride) {
+      const uint4 x = ld_stream4(v4 + i);
+      count(x.x); count(x.y); count(x.z); count(x.w);
+    }
   }
   for (size_t z = size_t(blockIdx.x) * THREADS + tid; z < a.zero_vec4; z += stride)
     a.zero_ptr[z] = make_uint4(0u, 0u, 0u, 0u);
@@ -196,8 +231,9 @@ static cudaError_t launch_scan(const ScanArgs& a, unsigned grid, cudaStream_t s)
 template <int THREADS>
 static cudaError_t launch_hist_lanes(const HistArgs& a, unsigned grid, cudaStream_t s) {
   const size_t smem = size_t(a.num_digits) * 256 * 32 * 4;
-  if (is_identity(a.xform)) upfront_hist_lanes_kernel<THREADS, false><<<grid, THREADS, smem, s>>>(a);
-  else upfront_hist_lanes_kernel<THREADS, true><<<grid, THREADS, smem, s>>>(a);
+  if (a.keys64) upfront_hist_lanes_kernel<THREADS, false, true><<<grid, THREADS, smem, s>>>(a);
+  else if (is_identity(a.xform)) upfront_hist_lanes_kernel<THREADS, false, false><<<grid, THREADS, smem, s>>>(a);
+  else upfront_hist_lanes_kernel<THREADS, true, false><<<grid, THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -207,8 +243,9 @@ static const HistKernel kHist11 = {11, 512, size_t(2) * 3 * 2048 * 4, &launch_hi
                                    reinterpret_cast<const void*>(&upfront_hist_kernel<11, 512, 2, false>),
                                    reinterpret_cast<const void*>(&upfront_hist_kernel<11, 512, 2, true>)};
 static const HistKernel kHist8 = {8, 1024, size_t(4) * 256 * 32 * 4, &launch_hist_lanes<1024>,
-                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024, false>),
-                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024, true>)};
+                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024, false, false>),
+                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024, true, false>),
+                                  reinterpret_cast<const void*>(&upfront_hist_lanes_kernel<1024, false, true>)};
 static const ScanKernel kScan11 = {11, 1024, &launch_scan<11>};
 static const ScanKernel kScan8 = {8, 256, &launch_scan<8>};
 

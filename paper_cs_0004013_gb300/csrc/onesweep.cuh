@@ -314,10 +314,22 @@ struct TileJob {
 
 // One tile of an LSD pass (steps 1-6 above).  The rank tables must be zero
 // on entry (the caller clears them and synchronises the block).
+// Interleaved two-word elements of the first and the last executed pass (in
+// and out are null on the other passes): 64-bit keys, whose word `high` is
+// this pass's key and whose other word rides as payload word 1, or 64-bit
+// values, payload words 1 and 2.
+struct PairIO {
+  const uint2* in;
+  uint2* out;
+  int key;        // 1: 64-bit keys; 0: 64-bit values
+  uint32_t high;  // 64-bit keys: this pass's digit lies in the high word
+  KeyXform64 x;   // 64-bit keys: their order map
+};
+
 template <int R, int THREADS, int ITEMS, int NV, typename S, bool EARLY_LB>
 __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t* kin, uint32_t* kout,
                                               const uint32_t* vin, uint32_t* vout, const uint32_t* vin2,
-                                              uint32_t* vout2, uint32_t shift, uint32_t width,
+                                              uint32_t* vout2, const PairIO& pio, uint32_t shift, uint32_t width,
                                               S* status, uint32_t parity, uint32_t* err, KeyXform xin, KeyXform xout,
                                               unsigned char* smem) {
   using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
@@ -337,7 +349,28 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   uint32_t key[ITEMS];
   const size_t wbase = job.base + size_t(warp) * 32 * ITEMS + lane;
   const size_t wend = job.base + valid;
-  if (valid == TILE) {
+  // 64-bit keys read interleaved keep the other word of their order map in
+  // the first payload section of the staging buffer, at the key's place in
+  // the tile, while the rank tables are in use (they fit below it); where
+  // they do not fit, the payload stage reads the word again (from L2).
+  constexpr bool STASH = L::RANK_BYTES <= size_t(TILE) * 4;
+  const uint32_t stash = TILE + warp * 32 * ITEMS + lane;
+  if (NV >= 1 && pio.key && pio.in) {
+    uint2 m[ITEMS];  // every load in flight before the first use
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const size_t idx = wbase + j * 32;
+      m[j] = (valid == TILE || idx < wend) ? ld_stream2(pio.in + idx) : make_uint2(0xffffffffu, 0xffffffffu);
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      // past the end: the largest key (its map is never taken)
+      const size_t idx = wbase + j * 32;
+      if (valid == TILE || idx < wend) m[j] = map64(m[j], pio.x);
+      key[j] = pio.high ? m[j].y : m[j].x;
+      if constexpr (STASH) s_buf[stash + j * 32] = pio.high ? m[j].x : m[j].y;
+    }
+  } else if (valid == TILE) {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) key[j] = ld_stream(kin + wbase + j * 32);
     if (!is_identity(xin)) {
@@ -438,22 +471,62 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) s_buf[(rk[j >> 1] >> (16 * (j & 1))) & 0xffffu] = key[j];
   // payload words, one at a time (each staged in its own TILE-word section)
+  bool staged = false;
+  if constexpr (NV >= 2) {
+    if (pio.in && !pio.key) {  // 64-bit values read interleaved: words 1 and 2, half a row at a time
+      constexpr int H = (ITEMS + 1) / 2;
 #pragma unroll
-  for (int w = 0; w < NV; ++w) {
-    const uint32_t* src = w == 0 ? vin : vin2;
-    uint32_t val[ITEMS];
-    if (valid == TILE) {
+      for (int h = 0; h < ITEMS; h += H) {
+        uint2 v2[H];
 #pragma unroll
-      for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(src + wbase + j * 32);
-    } else {
+        for (int j = 0; j < H; ++j) {
+          const size_t idx = wbase + (h + j) * 32;
+          v2[j] = (h + j < ITEMS && (valid == TILE || idx < wend)) ? ld_stream2(pio.in + idx) : make_uint2(0u, 0u);
+        }
 #pragma unroll
-      for (int j = 0; j < ITEMS; ++j) {
-        const size_t idx = wbase + j * 32;
-        val[j] = idx < wend ? src[idx] : 0u;
+        for (int j = 0; j < H; ++j) {
+          if (h + j < ITEMS) {
+            const uint32_t pos = (rk[(h + j) >> 1] >> (16 * ((h + j) & 1))) & 0xffffu;
+            s_buf[TILE + pos] = v2[j].x;
+            s_buf[2 * TILE + pos] = v2[j].y;
+          }
+        }
       }
+      staged = true;
     }
+  }
+  if (!staged) {
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) s_buf[(1 + w) * TILE + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = val[j];
+    for (int w = 0; w < NV; ++w) {
+      const uint32_t* src = w == 0 ? vin : vin2;
+      uint32_t val[ITEMS];
+      if (w == 0 && pio.key && pio.in) {  // the other word of an interleaved 64-bit key
+        if constexpr (STASH) {
+#pragma unroll
+          for (int j = 0; j < ITEMS; ++j) val[j] = s_buf[stash + j * 32];
+          __syncthreads();  // every stashed word is read before the section is overwritten
+        } else {
+#pragma unroll
+          for (int j = 0; j < ITEMS; ++j) {
+            const size_t idx = wbase + j * 32;
+            uint2 m = make_uint2(0u, 0u);
+            if (valid == TILE || idx < wend) m = map64(ld_stream2(pio.in + idx), pio.x);
+            val[j] = pio.high ? m.x : m.y;
+          }
+        }
+      } else if (valid == TILE) {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(src + wbase + j * 32);
+      } else {
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) {
+          const size_t idx = wbase + j * 32;
+          val[j] = idx < wend ? src[idx] : 0u;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) s_buf[(1 + w) * TILE + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = val[j];
+    }
   }
   if constexpr (!EARLY_LB) do_lookback();
   __syncthreads();
@@ -464,8 +537,12 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   // Keys leave through the inverse of the order map when this pass writes
   // the final order (the loop is written twice so that the identity case
   // pays nothing).
+  // The last pass of an interleaved sort writes the two words of each
+  // element as one 8-byte store (PAIR 1: a 64-bit key, through the inverse of
+  // its order map; PAIR 2: a 64-bit value).
   bool oob = false;
-  auto write_out = [&](auto invert) {
+  auto write_out = [&](auto invert, auto pair) {
+    constexpr int PAIR = decltype(pair)::value;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const uint32_t i = k * THREADS + tid;
@@ -473,17 +550,43 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
         const uint32_t kk = s_buf[i];
         const uint32_t g = s_goff[digit_of(kk, shift, width)] + i;
         if (g >= job.out_start && g < job.out_end) {
-          kout[g] = decltype(invert)::value ? from_ordered(kk, xout) : kk;
-          if constexpr (NV >= 1) vout[g] = s_buf[TILE + i];
-          if constexpr (NV >= 2) vout2[g] = s_buf[2 * TILE + i];
+          if constexpr (PAIR == 1) {
+            const uint32_t o = s_buf[TILE + i];
+            pio.out[g] = unmap64(pio.high ? make_uint2(o, kk) : make_uint2(kk, o), pio.x);
+            if constexpr (NV >= 2) vout2[g] = s_buf[2 * TILE + i];
+          } else {
+            kout[g] = decltype(invert)::value ? from_ordered(kk, xout) : kk;
+            if constexpr (PAIR == 2) {
+              pio.out[g] = make_uint2(s_buf[TILE + i], s_buf[2 * TILE + i]);
+            } else {
+              if constexpr (NV >= 1) vout[g] = s_buf[TILE + i];
+              if constexpr (NV >= 2) vout2[g] = s_buf[2 * TILE + i];
+            }
+          }
         } else {
           oob = true;
         }
       }
     }
   };
-  if (is_identity(xout)) write_out(std::false_type{});
-  else write_out(std::true_type{});
+  using P0 = std::integral_constant<int, 0>;
+  if constexpr (NV >= 1) {
+    if (pio.out && pio.key) {
+      write_out(std::false_type{}, std::integral_constant<int, 1>{});
+      if (oob) atomicOr(err, kErrBounds);
+      return;
+    }
+  }
+  if constexpr (NV >= 2) {
+    if (pio.out) {
+      if (is_identity(xout)) write_out(std::false_type{}, std::integral_constant<int, 2>{});
+      else write_out(std::true_type{}, std::integral_constant<int, 2>{});
+      if (oob) atomicOr(err, kErrBounds);
+      return;
+    }
+  }
+  if (is_identity(xout)) write_out(std::false_type{}, P0{});
+  else write_out(std::true_type{}, P0{});
   if (oob) atomicOr(err, kErrBounds);
 }
 
@@ -518,6 +621,11 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
     vin2 = route.src == BUF_IN ? a.vals2_in : (route.src == BUF_OUT ? a.vals2_out : a.vals2_alt);
     vout2 = route.dst == BUF_OUT ? a.vals2_out : a.vals2_alt;
   }
+  PairIO pio{nullptr, nullptr, a.pair_key, a.key_high, a.x64};
+  if constexpr (NV >= 1) {
+    if (route.src == BUF_IN) pio.in = a.pair_in;
+    if (route.last) pio.out = a.pair_out;
+  }
   const uint32_t tile = begin_tile<R, THREADS, ITEMS, NV>(a.tile_counter, smem);
   TileJob job;
   job.tile = tile;
@@ -528,7 +636,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   job.out_start = 0;
   job.out_end = a.n;
   job.bases = a.bases;
-  onesweep_tile<R, THREADS, ITEMS, NV, S, EARLY_LB>(job, kin, kout, vin, vout, vin2, vout2, a.shift, a.width,
+  onesweep_tile<R, THREADS, ITEMS, NV, S, EARLY_LB>(job, kin, kout, vin, vout, vin2, vout2, pio, a.shift, a.width,
                                                         reinterpret_cast<S*>(a.status), route.parity, a.err,
                                                         route.src == BUF_IN ? a.xin : KeyXform{0u, 0u},
                                                         route.last ? a.xout : KeyXform{0u, 0u}, smem);

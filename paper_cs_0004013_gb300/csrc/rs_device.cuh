@@ -39,6 +39,17 @@ __device__ __forceinline__ uint32_t from_ordered(uint32_t t, KeyXform x) {
 }
 __host__ __device__ __forceinline__ bool is_identity(KeyXform x) { return (x.fmask | x.smask) == 0u; }
 
+// The same map for 64-bit keys held as (low, high) words: the sign is the top
+// bit of the high word, and a set sign flips the low word by flo.
+__device__ __forceinline__ uint2 map64(uint2 k, KeyXform64 x) {
+  const uint32_t neg = uint32_t(int32_t(k.y) >> 31);  // all ones for a set sign bit
+  return make_uint2(k.x ^ (neg & x.flo), k.y ^ ((neg & x.fhi) ^ x.shi));
+}
+__device__ __forceinline__ uint2 unmap64(uint2 t, KeyXform64 x) {
+  const uint32_t neg = uint32_t(~int32_t(t.y) >> 31);  // the original sign is the complement of the top bit
+  return make_uint2(t.x ^ (neg & x.flo), t.y ^ ((neg & x.fhi) ^ x.shi));
+}
+
 // Digit of `width` bits at `shift` (width >= 1, shift + width <= 32).
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t shift, uint32_t width) {
   uint32_t r;
@@ -69,6 +80,11 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
   uint32_t v;
   asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint2 ld_stream2(const uint2* p) {
+  uint2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
   return v;
 }
 __device__ __forceinline__ uint4 ld_stream4(const uint4* p) {

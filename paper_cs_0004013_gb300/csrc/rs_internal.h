@@ -56,6 +56,12 @@ struct HistArgs {
   uint4* zero_ptr;     // region to clear (status words), may be null
   size_t zero_vec4;    // its size in 16-byte units
   KeyXform xform;      // applied to every key before its digits are taken
+  // 64-bit keys read interleaved (8-bit digits only): when keys64 is set the
+  // digits are taken from word `word64` (0 low, 1 high) of the key's order
+  // map x64, and `keys` is unused
+  const uint2* keys64;
+  uint32_t word64;
+  KeyXform64 x64;
 };
 
 // Exclusive scan of each digit's histogram + skip flags.
@@ -87,6 +93,17 @@ struct PassArgs {
   uint32_t* err;             // device error word
   KeyXform xin;              // applied to keys read from keys_in
   KeyXform xout;             // inverted on keys written to keys_out
+  // Interleaved two-word elements in place of two word planes (non-persistent
+  // kernels with payload words only).  The first executed pass reads them from
+  // pair_in, the last one writes them to pair_out; either may be null.
+  // pair_key = 1: 64-bit keys (order map x64); word key_high (0 low, 1 high)
+  // is this pass's key and the other word is payload word 1.  pair_key = 0:
+  // 64-bit values, payload words 1 and 2.
+  const uint2* pair_in;
+  uint2* pair_out;
+  int pair_key;
+  uint32_t key_high;
+  KeyXform64 x64;
 };
 
 struct OnesweepKernel {
@@ -112,6 +129,7 @@ struct HistKernel {
   cudaError_t (*launch)(const HistArgs&, unsigned grid, cudaStream_t);
   const void* func;     // the instance for unsigned keys
   const void* func_xf;  // the instance that maps keys of another kind first
+  const void* func_w64 = nullptr;  // the instance for interleaved 64-bit keys (if any)
 };
 
 struct ScanKernel {

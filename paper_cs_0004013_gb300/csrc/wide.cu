@@ -8,7 +8,9 @@
 // one routing of the eight passes (skipped digits included) keeps the planes
 // consistent.  These kernels split the interleaved input into the planes
 // (applying the order map of the key kind) and join the planes of the final
-// order back into interleaved keys (undoing it).
+// order back into interleaved keys (undoing it).  They serve the persistent
+// pass kernels; the tiled ones read and write the interleaved words
+// themselves in their first and last executed pass.
 #include <cuda_runtime.h>
 
 #include "rs_device.cuh"
@@ -17,16 +19,6 @@
 namespace rs {
 
 namespace {
-
-__device__ __forceinline__ uint2 map64(uint2 k, KeyXform64 x) {
-  const uint32_t neg = uint32_t(int32_t(k.y) >> 31);  // all ones for a set sign bit
-  return make_uint2(k.x ^ (neg & x.flo), k.y ^ ((neg & x.fhi) ^ x.shi));
-}
-
-__device__ __forceinline__ uint2 unmap64(uint2 t, KeyXform64 x) {
-  const uint32_t neg = uint32_t(~int32_t(t.y) >> 31);  // the original sign is the complement of the top bit
-  return make_uint2(t.x ^ (neg & x.flo), t.y ^ ((neg & x.fhi) ^ x.shi));
-}
 
 __global__ void __launch_bounds__(256) split_kernel(const WideArgs a) {
   const size_t stride = size_t(gridDim.x) * blockDim.x;

@@ -130,3 +130,27 @@ def test_u32_keys_u64_values(rs, kind, n):
     assert np.array_equal(ko.cpu().numpy().view(np.uint32), wk)
     assert np.array_equal(vo.cpu().numpy().view(np.uint64), wv)
     assert np.array_equal(offs, oracle.partition_offsets(n, 64))
+
+
+@pytest.mark.parametrize("tile", [0, 6])
+def test_keys_off_16_byte_boundary(rs, tile):
+    """Keys and values that start 8 bytes past a 16-byte boundary, odd
+    lengths: the interleaved reads take a head and a tail element apart
+    (tile 6 takes the split word planes instead)."""
+    import torch
+    n = 3 * TILE + 7
+    keys = _words(n + 1, 95)
+    d = torch.from_numpy(keys.view(np.int64).copy()).cuda()[1:]
+    assert d.data_ptr() % 16 == 8
+    out, _ = rs.sort64(d, plan={"tile": tile, "key_kind": KIND["f64"]})
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    assert np.array_equal(out.cpu().numpy().view(np.uint64), oracle.sort_keys(keys[1:], "f64"))
+    k32 = synth.uniform31(n, 96)
+    dv = torch.from_numpy(keys.view(np.int64).copy()).cuda()[1:]
+    ko, vo, _ = rs.sort_pairs64(torch.from_numpy(k32.view(np.int32)).cuda(), dv)
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk, wv = oracle.sort_pairs(k32, keys[1:], "u32")
+    assert np.array_equal(ko.cpu().numpy().view(np.uint32), wk)
+    assert np.array_equal(vo.cpu().numpy().view(np.uint64), wv)
