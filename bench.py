@@ -275,8 +275,14 @@ def run_ours(args):
     d_out = torch.empty_like(d_keys)
     plan = {"digit_bits": args.digit_bits, "tile": args.tile, "key_kind": KEY_KINDS[args.key_kind]}
     vals64 = args.vals64 and not wide
-    pairs = args.pairs or vals64
-    if vals64:
+    wide_v64 = args.vals64 and wide  # 64-bit keys with 64-bit values
+    pairs = args.pairs or args.vals64
+    if wide_v64:
+        d_vals = torch.arange(n, dtype=torch.int64, device=dev)
+        d_vout = torch.empty_like(d_vals)
+        temp = torch.empty(rs.rs_sort_u64_pairs64(None, None, None, None, n, plan=plan), dtype=torch.uint8,
+                           device=dev)
+    elif vals64:
         d_vals = torch.arange(n, dtype=torch.int64, device=dev)
         d_vout = torch.empty_like(d_vals)
         temp = torch.empty(rs.rs_sort_u32_pairs64(None, None, None, None, n, plan=plan), dtype=torch.uint8,
@@ -299,7 +305,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        if vals64:
+        if wide_v64:
+            rs.rs_sort_u64_pairs64(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
+        elif vals64:
             rs.rs_sort_u32_pairs64(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
         elif wide and pairs:
             rs.rs_sort_u64_pairs(d_keys, d_vals, d_out, d_vout, n, 64, plan, temp, stream, want_offsets=True)
@@ -375,7 +383,9 @@ def run_ours(args):
     # plane.  64-bit values that are split and joined add the same 32 B.
     split = "split64" in trace
     if wide:
-        bpk = (32 + 8 if split else 16) + passes * word_bytes
+        # 64-bit values: the passes carry an index; the last one reads each
+        # value (8 B) and writes it (8 B)
+        bpk = (32 + 8 if split else 16) + passes * word_bytes + (16 if wide_v64 else 0)
     else:
         bpk = (32 if split else 0) + 4 + passes * word_bytes
     peak, peak_kind = measured_peak()
@@ -385,7 +395,8 @@ def run_ours(args):
         avg_ms = tr["total_ms"] / tr["launches"]
         bytes_launch = word_bytes * tr["keys"] / tr["launches"]
         achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
-        key = f"{pass_kind}_{'keys64' if wide else ('pairs64' if vals64 else 'pairs' if pairs else 'keys')}_n{n}"
+        key = (f"{pass_kind}_{('keys64v64' if wide_v64 else 'keys64') if wide else ('pairs64' if vals64 else 'pairs' if pairs else 'keys')}"
+               f"_n{n}")
         traffic = traffic_from_profiles("onesweep.cuh", key)
         roof = {"bound": "hbm", "kernel": pass_kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
@@ -470,7 +481,8 @@ def run_ours(args):
             "config": {"workload": (workload_label(n, pairs, args.key_kind).replace("key+payload", "key+64-bit value")
                                     if vals64 else workload_label(n, pairs, args.key_kind) if not wide else
                                     workload_label(n, pairs).replace("uint32 keys uniform in [0, 2^31-1]",
-                                                                     "uint64 keys uniform over all 2^64 values")),
+                                                                     "uint64 keys uniform over all 2^64 values")
+                                    .replace("key+payload", "key+64-bit value" if wide_v64 else "key+payload")),
                        "n": n, "digit_bits": args.digit_bits or "auto", "passes": passes,
                        "algorithmic_bytes_per_key": bpk,
                        "sort_roofline_frac": value / world * 1e9 * bpk / (peak * 1e9),

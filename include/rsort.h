@@ -168,8 +168,8 @@ rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in,
  * or 8, mode LSD (or 0), tile selects the key+payload tile shape, and
  * key_kind orders the 64-bit words as unsigned (RS_KEY_U32), two's-complement
  * signed (RS_KEY_I32) or IEEE-754 binary64 totalOrder (RS_KEY_F32).  Temp:
- * four n-word planes (six with the persistent tile shapes, which split the
- * keys into planes first) plus histograms and status.                       */
+ * four n-word planes (six with the tile shapes other than the default,
+ * which split the keys into planes first) plus histograms and status.      */
 rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n,
                       uint32_t num_parts, uint64_t* h_part_offsets,
                       const rs_plan* plan, void* temp, size_t* temp_bytes,
@@ -204,6 +204,20 @@ rs_status rs_sort_u64_pairs(const uint64_t* keys_in, const uint32_t* vals_in,
                             uint32_t num_parts, uint64_t* h_part_offsets,
                             const rs_plan* plan, void* temp, size_t* temp_bytes,
                             rs_stream_t stream);
+
+/* rs_sort_u64 with a uint64 value per key (vals_in, vals_out: DEVICE, n
+ * each, 8-byte aligned, not overlapping the keys or each other): stable by
+ * key.  The passes carry each key's input index in place of its value (the
+ * first pass makes it, the last reads vals_in at it and writes the value to
+ * vals_out), so each pass moves three words per key as in rs_sort_u64_pairs.
+ * plan as for rs_sort_u64; tile shapes without an interleaved pass kernel
+ * (only the default has one) give RS_ERR_UNSUPPORTED.  Temp:
+ * rs_sort_u64_pairs's plus one n-word plane.                                */
+rs_status rs_sort_u64_pairs64(const uint64_t* keys_in, const uint64_t* vals_in,
+                              uint64_t* keys_out, uint64_t* vals_out, uint64_t n,
+                              uint32_t num_parts, uint64_t* h_part_offsets,
+                              const rs_plan* plan, void* temp, size_t* temp_bytes,
+                              rs_stream_t stream);
 
 /* ---- host buffers ------------------------------------------------------- */
 

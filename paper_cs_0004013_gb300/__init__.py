@@ -24,7 +24,7 @@ __all__ = [
     "rs_sort_u32", "rs_sort_u32_pairs", "rs_sort_u32_segmented", "rs_digit_histograms",
     "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_version", "rs_trace_enable",
     "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS", "rs_selftest_wait_timeout",
-    "rs_sort_u32_host", "rs_sort_u64", "sort64", "rs_sort_u64_pairs", "sort64_pairs", "rs_sort_u32_pairs64", "sort_pairs64", "rs_merge_u32", "merge",
+    "rs_sort_u32_host", "rs_sort_u64", "sort64", "rs_sort_u64_pairs", "rs_sort_u64_pairs64", "sort64_pairs", "rs_sort_u32_pairs64", "sort_pairs64", "rs_merge_u32", "merge",
     "sort", "sort_pairs", "sort_segmented", "temp_bytes", "part_offsets",
     "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD", "RS_KEY_U32", "RS_KEY_I32", "RS_KEY_F32",
 ]
@@ -74,6 +74,7 @@ _SIGS = {
     "rs_sort_u64": [_P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
     "rs_sort_u64_pairs": [_P, _P, _P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
     "rs_sort_u32_pairs64": [_P, _P, _P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
+    "rs_sort_u64_pairs64": [_P, _P, _P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
     "rs_merge_u32": [_P, _P, _U64, _P, _P, _U64, _P, _P, _U32, _U64P, _PLANP, _P, _SZP, _P],
     "rs_sort_u32_noalloc": [_P, _P, _U64, _U32, _U64P, _P],
     "rs_selftest_wait_timeout": [_P, ctypes.c_size_t, _P],
@@ -192,14 +193,29 @@ def rs_sort_u64_pairs(keys_in, vals_in, keys_out, vals_out, n: int, num_parts: i
     return tb.value if temp is None else offs
 
 
+def rs_sort_u64_pairs64(keys_in, vals_in, keys_out, vals_out, n: int, num_parts: int = 64, plan=None, temp=None,
+                        stream=None, want_offsets: bool = True):
+    """Calls rs_sort_u64_pairs64 (64-bit keys, 64-bit values); returns as
+    rs_sort_u32."""
+    tp, tb = _temp(temp)
+    offs = np.zeros(num_parts + 1, dtype=np.uint64) if (want_offsets and temp is not None) else None
+    op = offs.ctypes.data_as(_U64P) if offs is not None else None
+    _check(lib.rs_sort_u64_pairs64(_ptr(keys_in), _ptr(vals_in), _ptr(keys_out), _ptr(vals_out), n, num_parts,
+                                   op, _plan(plan), tp, ctypes.byref(tb),
+                                   _stream(stream) if temp is not None else None))
+    return tb.value if temp is None else offs
+
+
 def sort64_pairs(keys, vals, num_parts: int = 64, plan=None, stream=None):
-    """Stable (64-bit key, 32-bit value) sort of CUDA tensors: (keys, vals,
-    host partition offsets)."""
+    """Stable sort of CUDA tensors of 64-bit keys and 32-bit or (by the
+    values' element size) 64-bit values: (keys, vals, host partition
+    offsets)."""
     import torch
     n = keys.numel()
     ko, vo = torch.empty_like(keys), torch.empty_like(vals)
-    temp = _alloc_temp(rs_sort_u64_pairs(None, None, None, None, n, plan=plan), keys.device)
-    offs = rs_sort_u64_pairs(keys, vals, ko, vo, n, num_parts, plan, temp, stream)
+    call = rs_sort_u64_pairs64 if vals.element_size() == 8 else rs_sort_u64_pairs
+    temp = _alloc_temp(call(None, None, None, None, n, plan=plan), keys.device)
+    offs = call(keys, vals, ko, vo, n, num_parts, plan, temp, stream)
     return ko, vo, offs
 
 

@@ -194,6 +194,19 @@ rs_status pick_kernel(int R, uint32_t tile_idx, int vwords, bool wide, const One
               wide ? "64-bit" : "32-bit");
 }
 
+// The variant of a pass kernel that reads and writes interleaved 64-bit
+// words (same shape, payload words and status width), or null.
+const OnesweepKernel* pair_io_kernel(const OnesweepKernel* k) {
+  if (k->pair_io) return k;
+  int cnt = 0;
+  const OnesweepKernel* ks = k->radix_bits == 8 ? onesweep_kernels_r8(&cnt) : onesweep_kernels_r11(&cnt);
+  for (int i = 0; i < cnt; ++i)
+    if (ks[i].pair_io && ks[i].shape == k->shape && ks[i].vwords() == k->vwords() &&
+        ks[i].wide_status == k->wide_status)
+      return &ks[i];
+  return nullptr;
+}
+
 // The order map of a key kind (see KeyXform).
 rs_status key_xform(const rs_plan* user, KeyXform* out) {
   const uint32_t kind = user ? user->key_kind : uint32_t(RS_KEY_U32);
@@ -685,12 +698,13 @@ struct Layout64 {
   size_t status = 0, status_bytes = 0;
   size_t plane[6] = {};  // lo/hi words of the output, alternate and (split only) input order
   size_t val_alt = 0;    // the values' alternate plane (key+value sorts)
+  size_t idx_out = 0;    // 64-bit values: the index plane of the output order
   size_t memset_bytes = 0, total = 0;
 };
 
-Layout64 make_layout64(const SortPlan& p, uint64_t n, bool pairs) {
+Layout64 make_layout64(const SortPlan& p, uint64_t n, bool pairs, bool vals64 = false) {
   Layout64 L;
-  L.fused = p.k->persistent_per_sm == 0;
+  L.fused = pair_io_kernel(p.k) != nullptr;
   size_t off = 0;
   L.ctrl = off;
   off += kAlign;
@@ -710,6 +724,10 @@ Layout64 make_layout64(const SortPlan& p, uint64_t n, bool pairs) {
     L.val_alt = off;
     off = align_up(off + size_t(n) * 4);
   }
+  if (vals64) {
+    L.idx_out = off;
+    off = align_up(off + size_t(n) * 4);
+  }
   L.total = off;
   return L;
 }
@@ -724,14 +742,18 @@ rs_status key_xform64(const rs_plan* user, KeyXform64* out) {
   }
 }
 
+// vals64_in/out (fused layouts only): 64-bit values, sorted through an input
+// index that the passes carry as their second payload word.
 rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_in, const uint32_t* vals_in,
                     uint64_t* keys_out, uint32_t* vals_out, uint32_t n, KeyXform64 x, unsigned char* temp,
-                    DeviceState* ds, cudaStream_t s) {
+                    DeviceState* ds, cudaStream_t s, const uint64_t* vals64_in = nullptr,
+                    uint64_t* vals64_out = nullptr) {
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + L.ctrl);
   uint32_t* hist = reinterpret_cast<uint32_t*>(temp + L.hist);
   uint32_t* bases = reinterpret_cast<uint32_t*>(temp + L.bases);
   uint32_t* pl[6] = {};
   for (int i = 0; i < (L.fused ? 4 : 6); ++i) pl[i] = reinterpret_cast<uint32_t*>(temp + L.plane[i]);
+  const OnesweepKernel* pk = L.fused ? pair_io_kernel(p.k) : p.k;
   uint32_t *lo_out = pl[0], *hi_out = pl[1], *lo_alt = pl[2], *hi_alt = pl[3], *lo_in = pl[4], *hi_in = pl[5];
   const uint2* k2 = reinterpret_cast<const uint2*>(keys_in);
   RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, L.memset_bytes, s); }),
@@ -778,6 +800,12 @@ rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_i
       pa.vals2_in = vals_in;
       pa.vals2_out = vals_out;
       pa.vals2_alt = reinterpret_cast<uint32_t*>(temp + L.val_alt);
+    } else if (vals64_in) {  // so does the input index of a 64-bit value
+      pa.vals2_out = reinterpret_cast<uint32_t*>(temp + L.idx_out);
+      pa.vals2_alt = reinterpret_cast<uint32_t*>(temp + L.val_alt);
+      pa.iota = 1;
+      pa.gather = reinterpret_cast<const uint2*>(vals64_in);
+      pa.gather_out = reinterpret_cast<uint2*>(vals64_out);
     }
     pa.n = n;
     pa.shift = uint32_t(8 * (j % 4));
@@ -798,7 +826,7 @@ rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_i
       pa.key_high = high ? 1u : 0u;
       pa.x64 = x;
     }
-    RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }), "launch onesweep (64-bit)");
+    RS_CUDA(traced(T_PASS8, n, s, [&] { return pk->launch(pa, pass_grid(p, ds), s); }), "launch onesweep (64-bit)");
   }
   if (!L.fused) {  // the last executed pass always writes the output planes
     WideArgs ja{nullptr, reinterpret_cast<uint2*>(keys_out), lo_out, hi_out, n, x};
@@ -850,9 +878,11 @@ rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in, ui
                    reinterpret_cast<cudaStream_t>(stream), true);
 }
 
-static rs_status sort64_impl(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
-                             uint32_t* vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
-                             const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream, bool pairs) {
+// vbytes: 0 (keys only), 4 (uint32 values) or 8 (uint64 values).
+static rs_status sort64_impl(const uint64_t* keys_in, const void* vals_in, uint64_t* keys_out, void* vals_out,
+                             uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets, const rs_plan* plan,
+                             void* temp, size_t* temp_bytes, rs_stream_t stream, int vbytes) {
+  const bool pairs = vbytes != 0;
   g_last_error.clear();
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (!temp_bytes) return fail(RS_ERR_INVALID, "temp_bytes is NULL");
@@ -869,7 +899,9 @@ static rs_status sort64_impl(const uint64_t* keys_in, const uint32_t* vals_in, u
   q.key_kind = RS_KEY_U32;
   SortPlan p;
   if (rs_status st = make_plan(n, true, &q, &p, pairs ? 2 : 1); st != RS_OK) return st;
-  const Layout64 L = make_layout64(p, n, pairs);
+  const Layout64 L = make_layout64(p, n, pairs, vbytes == 8);
+  if (vbytes == 8 && !L.fused)
+    return fail(RS_ERR_UNSUPPORTED, "64-bit values: tile shape %u has no interleaved pass kernel", q.tile);
   if (!temp) {
     *temp_bytes = L.total;
     return RS_OK;
@@ -885,10 +917,10 @@ static rs_status sort64_impl(const uint64_t* keys_in, const uint32_t* vals_in, u
     if (overlaps(keys_out, nb, temp, L.total) || overlaps(keys_in, nb, temp, L.total))
       return fail(RS_ERR_INVALID, "a key buffer overlaps temp");
     if (pairs) {
-      const size_t vb = size_t(n) * 4;
+      const size_t vb = size_t(n) * vbytes;
       if (!vals_in || !vals_out) return fail(RS_ERR_INVALID, "NULL value buffer");
-      if ((reinterpret_cast<uintptr_t>(vals_in) | reinterpret_cast<uintptr_t>(vals_out)) & 3)
-        return fail(RS_ERR_INVALID, "value buffers must be 4-byte aligned");
+      if ((reinterpret_cast<uintptr_t>(vals_in) | reinterpret_cast<uintptr_t>(vals_out)) & (vbytes - 1))
+        return fail(RS_ERR_INVALID, "value buffers must be %d-byte aligned", vbytes);
       if (overlaps(vals_out, vb, vals_in, vb) || overlaps(vals_out, vb, keys_in, nb) ||
           overlaps(vals_out, vb, keys_out, nb) || overlaps(vals_out, vb, temp, L.total) ||
           overlaps(keys_out, nb, vals_in, vb))
@@ -899,22 +931,32 @@ static rs_status sort64_impl(const uint64_t* keys_in, const uint32_t* vals_in, u
   if (n == 0) return RS_OK;
   DeviceState* ds = nullptr;
   if (rs_status st = device_state(&ds); st != RS_OK) return st;
-  return run_lsd64(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n), x,
-                   static_cast<unsigned char*>(temp), ds, s);
+  if (vbytes == 8)
+    return run_lsd64(p, L, keys_in, nullptr, keys_out, nullptr, uint32_t(n), x, static_cast<unsigned char*>(temp), ds,
+                     s, static_cast<const uint64_t*>(vals_in), static_cast<uint64_t*>(vals_out));
+  return run_lsd64(p, L, keys_in, static_cast<const uint32_t*>(vals_in), keys_out, static_cast<uint32_t*>(vals_out),
+                   uint32_t(n), x, static_cast<unsigned char*>(temp), ds, s);
 }
 
 rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n, uint32_t num_parts,
                       uint64_t* h_part_offsets, const rs_plan* plan, void* temp, size_t* temp_bytes,
                       rs_stream_t stream) {
   return sort64_impl(keys_in, nullptr, keys_out, nullptr, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
-                     stream, false);
+                     stream, 0);
 }
 
 rs_status rs_sort_u64_pairs(const uint64_t* keys_in, const uint32_t* vals_in, uint64_t* keys_out,
                             uint32_t* vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
                             const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
   return sort64_impl(keys_in, vals_in, keys_out, vals_out, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
-                     stream, true);
+                     stream, 4);
+}
+
+rs_status rs_sort_u64_pairs64(const uint64_t* keys_in, const uint64_t* vals_in, uint64_t* keys_out,
+                              uint64_t* vals_out, uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets,
+                              const rs_plan* plan, void* temp, size_t* temp_bytes, rs_stream_t stream) {
+  return sort64_impl(keys_in, vals_in, keys_out, vals_out, n, num_parts, h_part_offsets, plan, temp, temp_bytes,
+                     stream, 8);
 }
 
 rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in, uint32_t* keys_out,
@@ -938,7 +980,7 @@ rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in, 
   // A tiled pass kernel reads and writes the interleaved values itself
   // (fused); a persistent one takes planes split and joined by kernels.
   Layout L = make_layout(p, n, true);
-  const bool fused = p.k->persistent_per_sm == 0;
+  const bool fused = pair_io_kernel(p.k) != nullptr;
   const int nplanes = fused ? 3 : 5;
   size_t plane[5] = {};
   size_t off = L.total;
@@ -971,9 +1013,12 @@ rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in, 
   uint32_t* pl[5] = {};
   for (int i = 0; i < nplanes; ++i) pl[i] = reinterpret_cast<uint32_t*>(t + plane[i]);
   uint32_t *vlo_out = pl[0], *vhi_out = pl[1], *vhi_alt = pl[2], *vlo_in = pl[3], *vhi_in = pl[4];
-  if (fused)
-    return run_lsd(p, L, keys_in, nullptr, keys_out, vlo_out, uint32_t(n), t, false, ds, s, nullptr, vhi_out,
+  if (fused) {
+    SortPlan q2 = p;
+    q2.k = pair_io_kernel(p.k);
+    return run_lsd(q2, L, keys_in, nullptr, keys_out, vlo_out, uint32_t(n), t, false, ds, s, nullptr, vhi_out,
                    vhi_alt, reinterpret_cast<const uint2*>(vals_in), reinterpret_cast<uint2*>(vals_out));
+  }
   const unsigned egrid = unsigned(std::min<size_t>((size_t(n) + 255) / 256, size_t(ds->num_sms) * 8));
   const KeyXform64 ident{0u, 0u, 0u};
   WideArgs wa{reinterpret_cast<const uint2*>(vals_in), nullptr, vlo_in, vhi_in, n, ident};

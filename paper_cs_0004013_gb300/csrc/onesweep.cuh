@@ -318,15 +318,26 @@ struct TileJob {
 // and out are null on the other passes): 64-bit keys, whose word `high` is
 // this pass's key and whose other word rides as payload word 1, or 64-bit
 // values, payload words 1 and 2.
+// With iota, the first executed pass makes the last payload word the
+// element's index in the input; with gout, the last executed pass writes
+// gather[that index] to gout in its place (values sorted by an index that
+// the passes carry instead of the values themselves; kernels with two
+// payload words and 64-bit keys).
 struct PairIO {
   const uint2* in;
   uint2* out;
   int key;        // 1: 64-bit keys; 0: 64-bit values
   uint32_t high;  // 64-bit keys: this pass's digit lies in the high word
   KeyXform64 x;   // 64-bit keys: their order map
+  int iota;
+  const uint2* gather;
+  uint2* gout;
+  uint32_t n;     // bound of a gathered index
 };
 
-template <int R, int THREADS, int ITEMS, int NV, typename S, bool EARLY_LB>
+// PIO: the PairIO paths are compiled in (kernels of the 64-bit sorts); the
+// plain kernels carry none of that code.
+template <int R, int THREADS, int ITEMS, int NV, typename S, bool EARLY_LB, bool PIO = false>
 __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t* kin, uint32_t* kout,
                                               const uint32_t* vin, uint32_t* vout, const uint32_t* vin2,
                                               uint32_t* vout2, const PairIO& pio, uint32_t shift, uint32_t width,
@@ -355,7 +366,7 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   // they do not fit, the payload stage reads the word again (from L2).
   constexpr bool STASH = L::RANK_BYTES <= size_t(TILE) * 4;
   const uint32_t stash = TILE + warp * 32 * ITEMS + lane;
-  if (NV >= 1 && pio.key && pio.in) {
+  if (PIO && NV >= 1 && pio.key && pio.in) {
     uint2 m[ITEMS];  // every load in flight before the first use
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
@@ -472,7 +483,7 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   for (int j = 0; j < ITEMS; ++j) s_buf[(rk[j >> 1] >> (16 * (j & 1))) & 0xffffu] = key[j];
   // payload words, one at a time (each staged in its own TILE-word section)
   bool staged = false;
-  if constexpr (NV >= 2) {
+  if constexpr (PIO && NV >= 2) {
     if (pio.in && !pio.key) {  // 64-bit values read interleaved: words 1 and 2, half a row at a time
       constexpr int H = (ITEMS + 1) / 2;
 #pragma unroll
@@ -500,7 +511,10 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
     for (int w = 0; w < NV; ++w) {
       const uint32_t* src = w == 0 ? vin : vin2;
       uint32_t val[ITEMS];
-      if (w == 0 && pio.key && pio.in) {  // the other word of an interleaved 64-bit key
+      if (PIO && NV >= 2 && w == NV - 1 && pio.iota) {  // the element's index in the input
+#pragma unroll
+        for (int j = 0; j < ITEMS; ++j) val[j] = uint32_t(wbase + j * 32);
+      } else if (PIO && w == 0 && pio.key && pio.in) {  // the other word of an interleaved 64-bit key
         if constexpr (STASH) {
 #pragma unroll
           for (int j = 0; j < ITEMS; ++j) val[j] = s_buf[stash + j * 32];
@@ -540,9 +554,18 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   // The last pass of an interleaved sort writes the two words of each
   // element as one 8-byte store (PAIR 1: a 64-bit key, through the inverse of
   // its order map; PAIR 2: a 64-bit value).
+  // GATHER (64-bit keys): the second payload word is an input index, and
+  // gather[index] goes out in its place (an index out of range is skipped
+  // and reported).  These are random reads; issuing several before their
+  // stores measured no faster.
   bool oob = false;
-  auto write_out = [&](auto invert, auto pair) {
+  auto gather_put = [&](uint32_t g, uint32_t ix) {
+    if (ix < pio.n) pio.gout[g] = ld_stream2(pio.gather + ix);
+    else oob = true;
+  };
+  auto write_out = [&](auto invert, auto pair, auto gather) {
     constexpr int PAIR = decltype(pair)::value;
+    constexpr bool GATHER = decltype(gather)::value;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const uint32_t i = k * THREADS + tid;
@@ -553,7 +576,10 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
           if constexpr (PAIR == 1) {
             const uint32_t o = s_buf[TILE + i];
             pio.out[g] = unmap64(pio.high ? make_uint2(o, kk) : make_uint2(kk, o), pio.x);
-            if constexpr (NV >= 2) vout2[g] = s_buf[2 * TILE + i];
+            if constexpr (NV >= 2) {
+              if constexpr (GATHER) gather_put(g, s_buf[2 * TILE + i]);
+              else vout2[g] = s_buf[2 * TILE + i];
+            }
           } else {
             kout[g] = decltype(invert)::value ? from_ordered(kk, xout) : kk;
             if constexpr (PAIR == 2) {
@@ -570,23 +596,25 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
     }
   };
   using P0 = std::integral_constant<int, 0>;
-  if constexpr (NV >= 1) {
+  using NG = std::false_type;
+  if constexpr (PIO && NV >= 1) {
     if (pio.out && pio.key) {
-      write_out(std::false_type{}, std::integral_constant<int, 1>{});
+      if (NV >= 2 && pio.gout) write_out(std::false_type{}, std::integral_constant<int, 1>{}, std::true_type{});
+      else write_out(std::false_type{}, std::integral_constant<int, 1>{}, NG{});
       if (oob) atomicOr(err, kErrBounds);
       return;
     }
   }
-  if constexpr (NV >= 2) {
+  if constexpr (PIO && NV >= 2) {
     if (pio.out) {
-      if (is_identity(xout)) write_out(std::false_type{}, std::integral_constant<int, 2>{});
-      else write_out(std::true_type{}, std::integral_constant<int, 2>{});
+      if (is_identity(xout)) write_out(std::false_type{}, std::integral_constant<int, 2>{}, NG{});
+      else write_out(std::true_type{}, std::integral_constant<int, 2>{}, NG{});
       if (oob) atomicOr(err, kErrBounds);
       return;
     }
   }
-  if (is_identity(xout)) write_out(std::false_type{}, P0{});
-  else write_out(std::true_type{}, P0{});
+  if (is_identity(xout)) write_out(std::false_type{}, P0{}, NG{});
+  else write_out(std::true_type{}, P0{}, NG{});
   if (oob) atomicOr(err, kErrBounds);
 }
 
@@ -603,7 +631,7 @@ __device__ __forceinline__ uint32_t begin_tile(uint32_t* counter, unsigned char*
 }
 
 // The plain pass: tile i covers keys [i * TILE, (i + 1) * TILE) of one array.
-template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB>
+template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, bool PIO>
 __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs a) {
   using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -621,10 +649,16 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
     vin2 = route.src == BUF_IN ? a.vals2_in : (route.src == BUF_OUT ? a.vals2_out : a.vals2_alt);
     vout2 = route.dst == BUF_OUT ? a.vals2_out : a.vals2_alt;
   }
-  PairIO pio{nullptr, nullptr, a.pair_key, a.key_high, a.x64};
-  if constexpr (NV >= 1) {
-    if (route.src == BUF_IN) pio.in = a.pair_in;
-    if (route.last) pio.out = a.pair_out;
+  PairIO pio{nullptr, nullptr, a.pair_key, a.key_high, a.x64, 0, a.gather, nullptr, a.n};
+  if constexpr (PIO && NV >= 1) {
+    if (route.src == BUF_IN) {
+      pio.in = a.pair_in;
+      pio.iota = a.iota;
+    }
+    if (route.last) {
+      pio.out = a.pair_out;
+      pio.gout = a.gather_out;
+    }
   }
   const uint32_t tile = begin_tile<R, THREADS, ITEMS, NV>(a.tile_counter, smem);
   TileJob job;
@@ -636,20 +670,21 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep_kernel(const PassArgs 
   job.out_start = 0;
   job.out_end = a.n;
   job.bases = a.bases;
-  onesweep_tile<R, THREADS, ITEMS, NV, S, EARLY_LB>(job, kin, kout, vin, vout, vin2, vout2, pio, a.shift, a.width,
+  onesweep_tile<R, THREADS, ITEMS, NV, S, EARLY_LB, PIO>(job, kin, kout, vin, vout, vin2, vout2, pio, a.shift,
+                                                             a.width,
                                                         reinterpret_cast<S*>(a.status), route.parity, a.err,
                                                         route.src == BUF_IN ? a.xin : KeyXform{0u, 0u},
                                                         route.last ? a.xout : KeyXform{0u, 0u}, smem);
 }
 
-template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB>
+template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, bool PIO>
 cudaError_t launch_onesweep(const PassArgs& a, unsigned grid, cudaStream_t s) {
   using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
-  onesweep_kernel<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB><<<grid, THREADS, L::SMEM, s>>>(a);
+  onesweep_kernel<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB, PIO><<<grid, THREADS, L::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB>
+template <int R, int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, bool PIO = false>
 OnesweepKernel make_onesweep(int shape_id) {
   using L = OnesweepLayout<R, THREADS, ITEMS, NV>;
   return OnesweepKernel{R,
@@ -660,10 +695,11 @@ OnesweepKernel make_onesweep(int shape_id) {
                         NV >= 1,
                         sizeof(S) == 8,
                         L::SMEM,
-                        &launch_onesweep<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB>,
-                        reinterpret_cast<const void*>(&onesweep_kernel<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB>),
+                        &launch_onesweep<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB, PIO>,
+                        reinterpret_cast<const void*>(&onesweep_kernel<R, THREADS, ITEMS, NV, S, MINB, EARLY_LB, PIO>),
                         0,
-                        NV};
+                        NV,
+                        PIO};
 }
 
 }  // namespace rs

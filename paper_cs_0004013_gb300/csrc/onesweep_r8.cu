@@ -12,8 +12,11 @@ using S64 = unsigned long long;
 static const OnesweepKernel kR8[] = {
     make_onesweep<8, 512, 16, false, S32, 2, false>(0), make_onesweep<8, 512, 16, true, S32, 2, false>(0),
     make_onesweep<8, 512, 16, false, S64, 2, false>(0), make_onesweep<8, 512, 16, true, S64, 2, false>(0),
-    // two payload words (64-bit keys with a value: the other key word and the value)
-    make_onesweep<8, 512, 16, 2, S32, 2, false>(0),     make_onesweep<8, 512, 16, 2, S64, 2, false>(0),
+    // two payload words (64-bit keys with a value: the other key word and the value),
+    // with the interleaved 64-bit reads and writes of the 64-bit sorts
+    make_onesweep<8, 512, 16, 2, S32, 2, false, true>(0), make_onesweep<8, 512, 16, 2, S64, 2, false, true>(0),
+    // the interleaved variants of the default key+payload kernel (64-bit keys)
+    make_onesweep<8, 512, 16, true, S32, 2, false, true>(0), make_onesweep<8, 512, 16, true, S64, 2, false, true>(0),
     make_onesweep<8, 512, 16, false, S32, 2, true>(1),  make_onesweep<8, 512, 16, true, S32, 2, true>(1),
     make_onesweep<8, 512, 24, false, S32, 2, false>(2), make_onesweep<8, 512, 24, true, S32, 2, false>(2),
     make_onesweep<8, 512, 24, false, S64, 2, false>(2),

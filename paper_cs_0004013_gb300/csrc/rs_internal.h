@@ -104,6 +104,13 @@ struct PassArgs {
   int pair_key;
   uint32_t key_high;
   KeyXform64 x64;
+  // Values sorted through an index (non-persistent kernels with two payload
+  // words): with iota the first executed pass makes the last payload word the
+  // element's input index; with gather_out the last executed pass writes
+  // gather[index] (n elements) to gather_out in its place.
+  int iota;
+  const uint2* gather;
+  uint2* gather_out;
 };
 
 struct OnesweepKernel {
@@ -119,6 +126,7 @@ struct OnesweepKernel {
   const void* func;  // kernel symbol (for attributes)
   int persistent_per_sm = 0;  // > 0: persistent kernel, grid = SMs x this (capped by tiles)
   int value_words = -1;       // payload words per key (-1: 1 if pairs else 0)
+  bool pair_io = false;       // reads and writes interleaved 64-bit words (PassArgs pair_* and gather fields)
   int vwords() const { return value_words >= 0 ? value_words : (pairs ? 1 : 0); }
 };
 

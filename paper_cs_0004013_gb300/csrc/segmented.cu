@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(THREADS, MINB) seg_pass_kernel(const SegPassAr
     job.out_start = jb.out_start;
     job.out_end = jb.out_end;
     job.bases = a.seg_bases + (size_t(jb.li) * a.num_digits + a.pass) * 256;
-    const PairIO none{nullptr, nullptr, 0, 0u, KeyXform64{0u, 0u, 0u}};
+    const PairIO none{nullptr, nullptr, 0, 0u, KeyXform64{0u, 0u, 0u}, 0, nullptr, nullptr, 0u};
     onesweep_tile<8, THREADS, ITEMS, PAIRS ? 1 : 0, uint32_t, false>(job, a.kin, a.kout, a.vin, a.vout, nullptr,
                                                                       nullptr, none, a.shift, a.width, a.status,
                                                                       a.parity, a.err, a.xin, a.xout, smem);

@@ -144,3 +144,22 @@ def test_host_entry_sizes_and_checks():
     st = r.lib.rs_sort_u32_host(None, None, None, None, 0, 64, offs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                 None, ctypes.c_void_p(1 << 28), ctypes.byref(sz), None)
     assert st == 0 and not offs.any()
+
+
+def test_wide_temp_queries():
+    """Temp of the 64-bit sorts: the default tile shape reads and writes
+    interleaved words (four key-word planes); other shapes split the keys
+    (six); 64-bit values add one index plane to the 32-bit-value layout."""
+    import paper_cs_0004013_gb300 as r
+    n = 1 << 22
+    k = r.rs_sort_u64(None, None, n)
+    kp = r.rs_sort_u64_pairs(None, None, None, None, n)
+    kp64 = r.rs_sort_u64_pairs64(None, None, None, None, n)
+    assert 16 * n <= k < kp < kp64
+    assert kp64 - kp >= 4 * n
+    # another key+payload shape (tile 6): split planes, two more per key word
+    assert r.rs_sort_u64(None, None, n, plan={"tile": 6}) >= k + 8 * n
+    with pytest.raises(r.RsError):
+        r.rs_sort_u64_pairs64(None, None, None, None, n, plan={"mode": 2})  # MSD is not offered for 64-bit keys
+    v64 = r.rs_sort_u32_pairs64(None, None, None, None, n)
+    assert v64 >= r.rs_sort_u32_pairs(None, None, None, None, n) + 12 * n

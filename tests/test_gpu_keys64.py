@@ -154,3 +154,60 @@ def test_keys_off_16_byte_boundary(rs, tile):
     wk, wv = oracle.sort_pairs(k32, keys[1:], "u32")
     assert np.array_equal(ko.cpu().numpy().view(np.uint32), wk)
     assert np.array_equal(vo.cpu().numpy().view(np.uint64), wv)
+
+
+def _check_pairs64(rs, keys, kind, plan=None, vals=None):
+    import torch
+    n = keys.size
+    if vals is None:
+        vals = synth.splitmix64(77 + n, n) ^ np.arange(n, dtype=np.uint64)  # distinct, every bit pattern
+    dk = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    dv = torch.from_numpy(vals.view(np.int64).copy()).cuda()
+    ko, vo, offs = rs.sort64_pairs(dk, dv, plan=dict(plan or {}, key_kind=KIND[kind]))
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk, wv = oracle.sort_pairs(keys, vals, kind)
+    assert np.array_equal(ko.cpu().numpy().view(np.uint64), wk)
+    assert np.array_equal(vo.cpu().numpy().view(np.uint64), wv)
+    assert np.array_equal(offs, oracle.partition_offsets(n, 64))
+    assert np.array_equal(dv.cpu().numpy().view(np.uint64), vals), "values modified"
+
+
+@pytest.mark.parametrize("kind", ["u64", "i64", "f64"])
+@pytest.mark.parametrize("n", [1, 2, 1000, 3 * TILE + 5, 1 << 20])
+def test_u64_keys_u64_values(rs, kind, n):
+    """64-bit keys carrying 64-bit values (rs_sort_u64_pairs64): the passes
+    carry an input index, the last one gathers the values; stable."""
+    _check_pairs64(rs, _words(n, 100 + n), kind)
+
+
+@pytest.mark.parametrize("kind", ["u64", "f64"])
+def test_u64_values_stable_and_skipped(rs, kind):
+    n = 300_007
+    r = synth.splitmix64(101, n)
+    _check_pairs64(rs, r % np.uint64(97) * np.uint64(0x0101010101010101), kind)  # few distinct keys
+    _check_pairs64(rs, r & np.uint64(0xFFFF00000000), kind)                    # six digits constant
+    _check_pairs64(rs, r & np.uint64(0xFF), kind)                              # seven digits constant
+    # every digit skipped: the one pass both makes the indices and gathers
+    _check_pairs64(rs, np.full(n, 0xC000000000000000, np.uint64), kind)
+
+
+def test_u64_values_unaligned_and_persistent(rs):
+    import torch
+    n = 2 * TILE + 3
+    keys = _words(n, 102)
+    vals = synth.splitmix64(103, n + 1)
+    dk = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    dv = torch.from_numpy(vals.view(np.int64).copy()).cuda()[1:]  # 8 bytes past a 16-byte boundary
+    ko, vo, _ = rs.sort64_pairs(dk, dv)
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk, wv = oracle.sort_pairs(keys, vals[1:], "u64")
+    assert np.array_equal(ko.cpu().numpy().view(np.uint64), wk)
+    assert np.array_equal(vo.cpu().numpy().view(np.uint64), wv)
+    for tile in range(1, 14):  # shapes without an interleaved two-payload-word kernel are refused on the host
+        try:
+            rs.rs_sort_u64_pairs64(None, None, None, None, 1000, plan={"tile": tile})
+        except rs.RsError:
+            continue
+        _check_pairs64(rs, keys, "u64", {"tile": tile})
