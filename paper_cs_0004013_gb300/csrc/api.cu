@@ -68,7 +68,7 @@ rs_status device_state(DeviceState** out) {
         RS_CUDA(cudaFuncSetAttribute(ks[i].func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks[i].smem)),
                 "cudaFuncSetAttribute(onesweep)");
       const HistKernel* h = hist_kernel(r);
-      for (const void* f : {h->func, h->func_xf, h->func_w64})
+      for (const void* f : h->funcs)
         if (f)
           RS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
                   "cudaFuncSetAttribute(hist)");

@@ -135,9 +135,7 @@ struct HistKernel {
   int threads;
   size_t smem;
   cudaError_t (*launch)(const HistArgs&, unsigned grid, cudaStream_t);
-  const void* func;     // the instance for unsigned keys
-  const void* func_xf;  // the instance that maps keys of another kind first
-  const void* func_w64 = nullptr;  // the instance for interleaved 64-bit keys (if any)
+  const void* funcs[6];  // every instance (for attributes); unused entries null
 };
 
 struct ScanKernel {
