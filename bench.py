@@ -377,15 +377,15 @@ def run_ours(args):
     passes = trace[pass_kind]["launches"] // args.steps if pass_kind else 0
     # per key and pass: read + write of the words moved
     word_bytes = 8 * ((2 if wide else 1) + (2 if vals64 else 1 if pairs else 0))
-    # 64-bit keys: the histograms read the interleaved keys twice (one launch
-    # per word); where the words are split into planes first, the split and
-    # the join (8 B read + 8 B written each) replace that by a read of each
-    # plane.  64-bit values that are split and joined add the same 32 B.
+    # 64-bit keys: the histograms read the interleaved keys once; where the
+    # words are split into planes first, the split and the join (8 B read +
+    # 8 B written each) come first and the histograms read each plane.
+    # 64-bit values that are split and joined add the same 32 B.
     split = "split64" in trace
     if wide:
         # 64-bit values: the passes carry an index; the last one reads each
         # value (8 B) and writes it (8 B)
-        bpk = (32 + 8 if split else 16) + passes * word_bytes + (16 if wide_v64 else 0)
+        bpk = (32 + 8 if split else 8) + passes * word_bytes + (16 if wide_v64 else 0)
     else:
         bpk = (32 if split else 0) + 4 + passes * word_bytes
     peak, peak_kind = measured_peak()

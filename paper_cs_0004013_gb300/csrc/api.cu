@@ -73,6 +73,7 @@ rs_status device_state(DeviceState** out) {
           RS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(h->smem)),
                   "cudaFuncSetAttribute(hist)");
     }
+    RS_CUDA(prepare_hist64(), "cudaFuncSetAttribute(hist64)");
     const SegKernels* sk = seg_kernels();
     const void* fn[8] = {sk->pass_keys,  sk->pass_pairs,  sk->tiny_keys, sk->tiny_pairs,
                          sk->small_keys, sk->small_pairs, sk->hist,      sk->hist_xf};
@@ -768,15 +769,19 @@ rs_status run_lsd64(const SortPlan& p, const Layout64& L, const uint64_t* keys_i
   const size_t work = (size_t(n) + 4095) / 4096;
   unsigned hgrid = unsigned(ds->num_sms);
   if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
-  for (int w = 0; w < 2; ++w) {
+  if (L.fused) {  // one read of the interleaved keys
     HistArgs ha{};
-    if (L.fused) {
-      ha.keys64 = k2;
-      ha.word64 = uint32_t(w);
-      ha.x64 = x;
-    } else {
-      ha.keys = w == 0 ? lo_in : hi_in;
-    }
+    ha.keys64 = k2;
+    ha.x64 = x;
+    ha.n = n;
+    ha.hist = hist;
+    ha.zero_ptr = reinterpret_cast<uint4*>(temp + L.status);
+    ha.zero_vec4 = L.status_bytes / 16;
+    RS_CUDA(traced(T_HIST, n, s, [&] { return launch_hist64(ha, hgrid, s); }), "launch upfront_hist64");
+  }
+  for (int w = 0; w < (L.fused ? 0 : 2); ++w) {
+    HistArgs ha{};
+    ha.keys = w == 0 ? lo_in : hi_in;
     ha.n = n;
     ha.num_digits = 4;
     for (int j = 0; j < 4; ++j) ha.dig[j] = DigitSpec{uint32_t(8 * j), 8u};

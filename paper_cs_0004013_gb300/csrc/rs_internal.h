@@ -56,11 +56,8 @@ struct HistArgs {
   uint4* zero_ptr;     // region to clear (status words), may be null
   size_t zero_vec4;    // its size in 16-byte units
   KeyXform xform;      // applied to every key before its digits are taken
-  // 64-bit keys read interleaved (8-bit digits only): when keys64 is set the
-  // digits are taken from word `word64` (0 low, 1 high) of the key's order
-  // map x64, and `keys` is unused
+  // launch_hist64 only: interleaved 64-bit keys and their order map
   const uint2* keys64;
-  uint32_t word64;
   KeyXform64 x64;
 };
 
@@ -135,7 +132,7 @@ struct HistKernel {
   int threads;
   size_t smem;
   cudaError_t (*launch)(const HistArgs&, unsigned grid, cudaStream_t);
-  const void* funcs[6];  // every instance (for attributes); unused entries null
+  const void* funcs[4];  // every instance (for attributes); unused entries null
 };
 
 struct ScanKernel {
@@ -282,6 +279,10 @@ void set_last_error(int status, const char* fmt, ...);
 const OnesweepKernel* onesweep_kernels_r8(int* count);
 const OnesweepKernel* onesweep_kernels_r11(int* count);
 const HistKernel* hist_kernel(int radix_bits);
+// All eight byte-digit histograms of interleaved 64-bit keys (HistArgs keys64,
+// x64; hist is [8][256]) in one read; prepare_hist64 sets its shared-memory size.
+cudaError_t launch_hist64(const HistArgs& a, unsigned grid, cudaStream_t s);
+cudaError_t prepare_hist64();
 const ScanKernel* scan_kernel(int radix_bits);
 
 }  // namespace rs

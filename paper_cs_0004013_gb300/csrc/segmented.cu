@@ -88,7 +88,10 @@ __device__ __forceinline__ uint32_t find_segment(const uint32_t* tile_prefix, ui
 // only touches shared-memory bank l (no atomic conflicts whatever the
 // digits); the copies are summed into the segment's global arrays when the
 // run moves on to the next segment, and at the end.  Also writes each
-// tile's job entry and clears its chained-scan status row.
+// tile's job entry and clears its chained-scan status row.  The digits are
+// the key's low num_digits bytes (the launcher checks): each is taken with
+// one byte permute and counted with one shared-memory reduction on a 32-bit
+// shared address (the count loop is bound by integer instructions).
 template <int THREADS, bool XF>
 __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs a) {
   extern __shared__ __align__(16) uint32_t sh[];  // [num_digits][256][32]
@@ -100,12 +103,8 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
   const uint32_t t_end = t_begin + per < total ? t_begin + per : total;
   if (t_begin >= t_end) return;  // uniform across the block
   for (int i = tid; i < nd * 256 * 32; i += THREADS) sh[i] = 0u;
-  uint32_t sft[kMaxDigits], wid[kMaxDigits];
-#pragma unroll
-  for (int j = 0; j < kMaxDigits; ++j) {
-    sft[j] = a.dig[j].shift;
-    wid[j] = a.dig[j].width;
-  }
+  // this lane's copy of bin 0 of digit 0; (digit j, bin b) is 32 KiB * j + 128 * b bytes further
+  const uint32_t lane_base = uint32_t(__cvta_generic_to_shared(sh)) + uint32_t(lane) * 4u;
   const KeyXform xf = a.xform;
   // sums a segment's lane copies into its global histograms and zeroes them;
   // each thread owns whole (digit, bin) rows and starts at its own lane, so
@@ -161,8 +160,13 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
         if (i0 + uint64_t(u) * THREADS >= end) break;
         const uint32_t kk = XF ? to_ordered(k[u], xf) : k[u];
 #pragma unroll
-        for (int j = 0; j < kMaxDigits; ++j)
-          if (j < nd) atomicAdd(&sh[(j * 256 + digit_of(kk, sft[j], wid[j])) * 32 + lane], 1u);
+        for (int j = 0; j < kMaxDigits; ++j) {
+          if (j < nd) {
+            const uint32_t b = __byte_perm(kk, 0u, 0x4440u + uint32_t(j));
+            const uint32_t addr = lane_base + uint32_t(j * 256 * 32 * 4) + b * 128u;
+            asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr) : "memory");
+          }
+        }
       }
     }
     // this tile's chained-scan status row starts out "not ready"
@@ -364,6 +368,9 @@ cudaError_t launch_seg_plan(const SegPlanArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_seg_hist(const SegHistArgs& a, unsigned grid, cudaStream_t s) {
+  if (a.num_digits < 1 || a.num_digits > kMaxDigits) return cudaErrorInvalidValue;
+  for (int j = 0; j < a.num_digits; ++j)  // the kernel counts the key's low bytes
+    if (a.dig[j].shift != uint32_t(8 * j) || a.dig[j].width != 8u) return cudaErrorInvalidValue;
   const size_t smem = size_t(a.num_digits) * 256 * 32 * 4;
   if (is_identity(a.xform)) seg_hist_kernel<kSegHistThreads, false><<<grid, kSegHistThreads, smem, s>>>(a);
   else seg_hist_kernel<kSegHistThreads, true><<<grid, kSegHistThreads, smem, s>>>(a);
