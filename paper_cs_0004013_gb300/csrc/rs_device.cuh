@@ -50,11 +50,11 @@ __device__ __forceinline__ uint2 unmap64(uint2 t, KeyXform64 x) {
   return make_uint2(t.x ^ (neg & x.flo), t.y ^ ((neg & x.fhi) ^ x.shi));
 }
 
-// Digit of `width` bits at `shift` (width >= 1, shift + width <= 32).
+// Digit of `width` bits at `shift` (1 <= width <= 31, shift + width <= 32):
+// a shift and a mask (the mask is loop-invariant and hoisted by the compiler;
+// a bit-field extract with run-time operands takes more instructions).
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, uint32_t shift, uint32_t width) {
-  uint32_t r;
-  asm("bfe.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(key), "r"(shift), "r"(width));
-  return r;
+  return (key >> shift) & ((1u << width) - 1u);
 }
 
 // ---- relaxed, gpu-scope accesses for the cross-tile status words ----------
