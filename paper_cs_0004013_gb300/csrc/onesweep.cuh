@@ -264,20 +264,20 @@ __device__ __forceinline__ void lookback(const S* st, uint32_t tile, uint32_t fi
 template <int R, int ITEMS>
 __device__ __forceinline__ void warp_rank(const uint32_t (&key)[ITEMS], uint32_t shift, uint32_t width, uint32_t* wm,
                                           uint16_t* wc, uint32_t (&rk)[(ITEMS + 1) / 2]) {
+  static_assert(R <= 16, "two digits share the uniformity test word");
   const int lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt(), gt = lanemask_gt();
-#pragma unroll
-  for (int j = 0; j < ITEMS; ++j) {
-    const uint32_t d = digit_of(key[j], shift, width);
+  auto rank_one = [&](int j, uint32_t d, bool uniform) {
     uint32_t r;
-    if (__all_sync(0xffffffffu, d == __shfl_sync(0xffffffffu, d, 0))) {
+    if (uniform) {
       const uint32_t before = wc[d];
       __syncwarp();
       if (lane == 31) wc[d] = uint16_t(before + 32u);
       __syncwarp();
       r = before + lane;
     } else {
-      const uint32_t lo = d & (kMaskSlots - 1u);
+      // digits of at most kMaskBits bits index the table directly
+      const uint32_t lo = R <= kMaskBits ? d : (d & (kMaskSlots - 1u));
       uint32_t same_hi = 0xffffffffu;
 #pragma unroll
       for (int b = kMaskBits; b < R; ++b) {
@@ -298,6 +298,18 @@ __device__ __forceinline__ void warp_rank(const uint32_t (&key)[ITEMS], uint32_t
     }
     if (j & 1) rk[j >> 1] |= r << 16;
     else rk[j >> 1] = r;
+  };
+  // Items two at a time: one shuffle and one vote tell whether both digits
+  // are the same in every lane (then the counters move by 32 without the
+  // mask table); otherwise both take the table, which is right either way.
+#pragma unroll
+  for (int j = 0; j < ITEMS; j += 2) {
+    const uint32_t d0 = digit_of(key[j], shift, width);
+    const uint32_t d1 = j + 1 < ITEMS ? digit_of(key[j + 1], shift, width) : d0;
+    const uint32_t pk = d0 | (d1 << 16);
+    const bool uniform = __all_sync(0xffffffffu, pk == __shfl_sync(0xffffffffu, pk, 0));
+    rank_one(j, d0, uniform);
+    if (j + 1 < ITEMS) rank_one(j + 1, d1, uniform);
   }
 }
 
@@ -559,6 +571,7 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   // and reported).  These are random reads; issuing several before their
   // stores measured no faster.
   bool oob = false;
+  const uint32_t span = job.out_end - job.out_start;
   auto gather_put = [&](uint32_t g, uint32_t ix) {
     if (ix < pio.n) pio.gout[g] = ld_stream2(pio.gather + ix);
     else oob = true;
@@ -572,7 +585,7 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
       if (valid == TILE || i < valid) {
         const uint32_t kk = s_buf[i];
         const uint32_t g = s_goff[digit_of(kk, shift, width)] + i;
-        if (g >= job.out_start && g < job.out_end) {
+        if (g - job.out_start < span) {  // out_start <= g < out_end
           if constexpr (PAIR == 1) {
             const uint32_t o = s_buf[TILE + i];
             pio.out[g] = unmap64(pio.high ? make_uint2(o, kk) : make_uint2(kk, o), pio.x);
