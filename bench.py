@@ -456,12 +456,16 @@ def run_ours(args):
             barrier()
             return whole_job_rate(n, world, args.steps, max_over_ranks(e0.elapsed_time(e1), world, dev))
 
+        # the host link is shared with the machine's other work and its rate
+        # varies from run to run: the piped figure is the median of three
+        # measurements (all three are reported)
         serial = e2e_time(1)
-        piped = e2e_time(E2E_STREAMS)
+        piped_runs = [e2e_time(E2E_STREAMS) for _ in range(3)]
+        piped = statistics.median(piped_runs)
         rs.rs_check_device_error()
         per_step = (8 if pairs else 4) * n
         e2e = {"value": piped, "unit": "Gkeys/s", "h2d_bytes_per_step": per_step, "d2h_bytes_per_step": per_step,
-               "streams": E2E_STREAMS, "one_stream_value": serial,
+               "streams": E2E_STREAMS, "repeats": piped_runs, "one_stream_value": serial,
                "api": "rs_sort_u32_host (pinned host buffers; copies of consecutive sorts overlap)"}
         for tmp, h_out, h_vout in slots:
             ok = np.array_equal(h_out.numpy().view(np.uint32)[:: max(1, n // 4096)],
