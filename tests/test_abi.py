@@ -163,3 +163,38 @@ def test_wide_temp_queries():
         r.rs_sort_u64_pairs64(None, None, None, None, n, plan={"mode": 2})  # MSD is not offered for 64-bit keys
     v64 = r.rs_sort_u32_pairs64(None, None, None, None, n)
     assert v64 >= r.rs_sort_u32_pairs(None, None, None, None, n) + 12 * n
+
+
+def test_wide_entries_reject_bad_buffers_before_any_launch():
+    """64-bit keys and values: misaligned or overlapping buffers are refused
+    on the host (fake device addresses; nothing is launched)."""
+    import paper_cs_0004013_gb300 as r
+    n = 1000
+    P = ctypes.c_void_p
+    need = r.rs_sort_u64_pairs64(None, None, None, None, n)
+    sz = ctypes.c_size_t(need)
+    keys_in, keys_out, vals_in, vals_out, temp = 1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 28
+    # values misaligned for 8-byte words
+    st = r.lib.rs_sort_u64_pairs64(P(keys_in), P(vals_in + 4), P(keys_out), P(vals_out), n, 64, None, None,
+                                   P(temp), ctypes.byref(sz), None)
+    assert st == 1 and "aligned" in r.rs_last_error()
+    # vals_out overlapping keys_out
+    st = r.lib.rs_sort_u64_pairs64(P(keys_in), P(vals_in), P(keys_out), P(keys_out + 4000), n, 64, None, None,
+                                   P(temp), ctypes.byref(sz), None)
+    assert st == 1 and "overlap" in r.rs_last_error()
+    # temp one byte short
+    short = ctypes.c_size_t(need - 1)
+    st = r.lib.rs_sort_u64_pairs64(P(keys_in), P(vals_in), P(keys_out), P(vals_out), n, 64, None, None,
+                                   P(temp), ctypes.byref(short), None)
+    assert st == 2
+    # 32-bit keys with 64-bit values: the same alignment rule
+    need = r.rs_sort_u32_pairs64(None, None, None, None, n)
+    sz = ctypes.c_size_t(need)
+    st = r.lib.rs_sort_u32_pairs64(P(keys_in), P(vals_in + 4), P(keys_out), P(vals_out), n, 64, None, None,
+                                   P(temp), ctypes.byref(sz), None)
+    assert st == 1 and "aligned" in r.rs_last_error()
+    # 64-bit keys must be 8-byte aligned
+    need = r.rs_sort_u64(None, None, n)
+    sz = ctypes.c_size_t(need)
+    st = r.lib.rs_sort_u64(P(keys_in + 4), P(keys_out), n, 64, None, None, P(temp), ctypes.byref(sz), None)
+    assert st == 1 and "aligned" in r.rs_last_error()
