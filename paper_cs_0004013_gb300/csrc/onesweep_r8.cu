@@ -20,6 +20,7 @@ static const OnesweepKernel kR8[] = {
     make_onesweep<8, 512, 16, false, S32, 2, true>(1),  make_onesweep<8, 512, 16, true, S32, 2, true>(1),
     make_onesweep<8, 512, 24, false, S32, 2, false>(2), make_onesweep<8, 512, 24, true, S32, 2, false>(2),
     make_onesweep<8, 512, 24, false, S64, 2, false>(2),
+    make_onesweep<8, 512, 24, true, S32, 2, false, true>(2),  // interleaved: 64-bit keys
     make_onesweep<8, 1024, 16, false, S32, 1, false>(3), make_onesweep<8, 1024, 16, true, S32, 1, false>(3),
     make_onesweep<8, 384, 20, false, S32, 2, false>(4), make_onesweep<8, 384, 20, true, S32, 2, false>(4),
     // persistent, software-pipelined (onesweep_pipe.cuh)
