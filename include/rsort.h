@@ -168,8 +168,9 @@ rs_status rs_sort_u32_pairs64(const uint32_t* keys_in, const uint64_t* vals_in,
  * or 8, mode LSD (or 0), tile selects the key+payload tile shape, and
  * key_kind orders the 64-bit words as unsigned (RS_KEY_U32), two's-complement
  * signed (RS_KEY_I32) or IEEE-754 binary64 totalOrder (RS_KEY_F32).  Temp:
- * four n-word planes (six with the tile shapes other than the default,
- * which split the keys into planes first) plus histograms and status.      */
+ * four n-word planes (six with the tile shapes other than 1 and 3, which
+ * split the keys into planes first) plus histograms and status.  The
+ * default tile is 3 above 2^22 keys (below 2^30 - 2^16), else 1.           */
 rs_status rs_sort_u64(const uint64_t* keys_in, uint64_t* keys_out, uint64_t n,
                       uint32_t num_parts, uint64_t* h_part_offsets,
                       const rs_plan* plan, void* temp, size_t* temp_bytes,
@@ -210,8 +211,8 @@ rs_status rs_sort_u64_pairs(const uint64_t* keys_in, const uint32_t* vals_in,
  * key.  The passes carry each key's input index in place of its value (the
  * first pass makes it, the last reads vals_in at it and writes the value to
  * vals_out), so each pass moves three words per key as in rs_sort_u64_pairs.
- * plan as for rs_sort_u64; tile shapes without an interleaved pass kernel
- * (only the default has one) give RS_ERR_UNSUPPORTED.  Temp:
+ * plan as for rs_sort_u64; tile shapes without an interleaved
+ * two-payload-word kernel (all but the default, 1) give RS_ERR_UNSUPPORTED.  Temp:
  * rs_sort_u64_pairs's plus one n-word plane.                                */
 rs_status rs_sort_u64_pairs64(const uint64_t* keys_in, const uint64_t* vals_in,
                               uint64_t* keys_out, uint64_t* vals_out, uint64_t n,
