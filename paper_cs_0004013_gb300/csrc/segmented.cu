@@ -130,7 +130,12 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
   uint32_t s = a.large_seg[li];
   uint64_t seg_start = a.seg_off[s], seg_end = a.seg_off[s + 1];
   __syncthreads();
-  for (uint32_t t = t_begin; t < t_end; ++t) {
+  // The block's tiles of one segment form one contiguous key range: it is
+  // counted in one sweep (whatever the tile size, every sweep iteration but
+  // the last keeps all loads busy), then the tiles' job entries are written
+  // and their status rows cleared.
+  uint32_t t = t_begin;
+  while (t < t_end) {
     if (t >= next) {  // uniform: every thread steps the same way
       flush(li);
       do {
@@ -142,22 +147,29 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
       seg_start = a.seg_off[s];
       seg_end = a.seg_off[s + 1];
     }
-    const uint64_t start = seg_start + uint64_t(t - first) * a.tile;
-    const uint64_t end = start + a.tile < seg_end ? start + a.tile : seg_end;
-    if (tid == 0)
-      a.jobs[t] = SegTileJob{start, uint32_t(end - start), first, uint32_t(seg_start), uint32_t(seg_end), li, 0u};
+    const uint32_t run_end = next < t_end ? next : t_end;  // this segment's tiles in the block's range
+    const uint64_t rs = seg_start + uint64_t(t - first) * a.tile;
+    const uint64_t re_full = seg_start + uint64_t(run_end - first) * a.tile;
+    const uint64_t re = re_full < seg_end ? re_full : seg_end;
+    for (uint32_t u = t + tid; u < run_end; u += THREADS) {
+      const uint64_t start = seg_start + uint64_t(u - first) * a.tile;
+      const uint64_t end = start + a.tile < seg_end ? start + a.tile : seg_end;
+      a.jobs[u] = SegTileJob{start, uint32_t(end - start), first, uint32_t(seg_start), uint32_t(seg_end), li, 0u};
+    }
+    // the tiles' chained-scan status rows start out "not ready"
+    for (size_t z = tid; z < size_t(run_end - t) * 256; z += THREADS) a.status[size_t(t) * 256 + z] = 0u;
     // eight loads in flight per thread before the counting (measured faster
-    // than two 16-byte vectors per thread, and than all of a tile's loads)
-    for (uint64_t i0 = start + tid; i0 < end; i0 += 8 * THREADS) {
+    // than two 16-byte vectors per thread)
+    for (uint64_t i0 = rs + tid; i0 < re; i0 += 8 * THREADS) {
       uint32_t k[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const uint64_t i = i0 + uint64_t(u) * THREADS;
-        k[u] = i < end ? ld_stream(a.keys + i) : 0u;
+        k[u] = i < re ? ld_stream(a.keys + i) : 0u;
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        if (i0 + uint64_t(u) * THREADS >= end) break;
+        if (i0 + uint64_t(u) * THREADS >= re) break;
         const uint32_t kk = XF ? to_ordered(k[u], xf) : k[u];
 #pragma unroll
         for (int j = 0; j < kMaxDigits; ++j) {
@@ -169,8 +181,7 @@ __global__ void __launch_bounds__(THREADS, 1) seg_hist_kernel(const SegHistArgs 
         }
       }
     }
-    // this tile's chained-scan status row starts out "not ready"
-    for (int i = tid; i < 256; i += THREADS) a.status[size_t(t) * 256 + i] = 0u;
+    t = run_end;
   }
   flush(li);
 }
@@ -331,7 +342,7 @@ cudaError_t launch_local(const LocalArgs& a, unsigned grid, cudaStream_t s) {
 // Tiled passes over large segments: 8-bit digits, 512 x 16 tiles.
 // Tiled passes over large segments: 512 x 24 tiles for keys, 512 x 16 with
 // payloads (the plain sort's best shapes).
-constexpr int kSegThreads = 512, kSegItemsKeys = 24, kSegItemsPairs = 16;
+constexpr int kSegThreads = 512, kSegItemsKeys = 24, kSegItemsPairs = 22;
 // Local sorts: tiny segments <= 256 x 16 keys, small ones <= 1024 x 16 keys.
 constexpr int kTinyThreads = 256, kSmallThreads = 1024, kLocalItems = 16;
 // Segment histograms: one 1024-thread block per SM (lane copies of up to

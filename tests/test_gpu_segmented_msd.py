@@ -38,7 +38,9 @@ def _segmented(rs, keys, sizes, pairs, num_parts=64):
 
 @pytest.mark.parametrize("pairs", [False, True])
 def test_segmented_all_classes(rs, pairs):
-    sizes = [0, 1, 2, 31, 4095, 4096, 4097, 0, 16383, 16384, 16385, 8192 * 3 + 5, 100_000, 1, 7, 250_001, 33]
+    # around the tiled passes' tile sizes too (12,288 keys, 11,264 pairs)
+    sizes = [0, 1, 2, 31, 4095, 4096, 4097, 0, 16383, 16384, 16385, 8192 * 3 + 5, 100_000, 1, 7, 250_001, 33,
+             3 * 12288 - 1, 3 * 12288 + 1, 2 * 11264 - 1, 2 * 11264, 2 * 11264 + 1]
     n = int(sum(sizes))
     _segmented(rs, synth.gauss_mix(n, 5), sizes, pairs)
 
