@@ -90,3 +90,38 @@ def test_merge_is_the_stable_sort_of_the_concatenation(a, b):
     keys, vals = a + b, va + vb
     want = sorted(range(len(keys)), key=lambda i: keys[i])
     assert list(vo) == [vals[i] for i in want] and list(ko) == [keys[i] for i in want]
+
+
+U64 = st.integers(min_value=0, max_value=2**64 - 1)
+
+
+@settings(**SETTINGS)
+@given(st.lists(st.integers(min_value=-2**63, max_value=2**63 - 1), max_size=200))
+def test_i64_order(ints):
+    w = np.array(ints, dtype=np.int64).view(np.uint64)
+    assert [int(x) for x in oracle.sort_keys(w, "i64").view(np.int64)] == sorted(ints)
+
+
+@settings(**SETTINGS)
+@given(st.lists(st.floats(width=64, allow_nan=False), max_size=200))
+def test_f64_order_is_numeric_with_negative_zero_first(vals):
+    w = np.array(vals, dtype=np.float64).view(np.uint64)
+    got = oracle.sort_keys(w, "f64")
+    f = got.view(np.float64)
+    assert np.all(f[1:] >= f[:-1])
+    neg = (got >> np.uint64(63)).astype(bool)
+    zs = neg[f == 0]
+    assert np.all(zs[:-1] >= zs[1:])  # every -0 before every +0
+    assert sorted(got.tolist()) == sorted(w.tolist())  # a permutation of the words
+
+
+@settings(**SETTINGS)
+@given(st.lists(st.tuples(U64, U64), max_size=200))
+def test_u64_pairs_carry_64_bit_values_stably(pairs):
+    keys = np.array([k for k, _ in pairs], dtype=np.uint64)
+    vals = np.array([v for _, v in pairs], dtype=np.uint64)
+    ko, vo = oracle.sort_pairs(keys, vals, "u64")
+    want = sorted(range(len(pairs)), key=lambda i: pairs[i][0])  # Python's sort is stable
+    assert [int(x) for x in ko] == [pairs[i][0] for i in want]
+    assert [int(x) for x in vo] == [pairs[i][1] for i in want]
+    assert vo.dtype == np.uint64
