@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -53,6 +54,7 @@ FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 126 * 1024 * 1024
 FLUSH_BYTES = 256 << 20
 E2E_STREAMS = 3
+CLOCK_SETTLE_S = 0.5
 
 
 def parse():
@@ -97,7 +99,8 @@ def dist_env():
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples every 200 ms while the timed region runs."""
+    """nvidia-smi samples every 200 ms, each stamped with the host time it
+    arrived, so that the samples of a time window can be picked out."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -105,6 +108,8 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
+        self.samples = []  # (time.monotonic() on arrival, csv line)
+        self._reader = None
 
     def __enter__(self):
         try:
@@ -113,23 +118,40 @@ class ClockSampler:
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+        if self.proc is not None:
+            self._reader = threading.Thread(target=self._read, daemon=True)
+            self._reader.start()
         return self
 
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.samples.append((time.monotonic(), line))
+
+    def wait_first(self, timeout_s: float = 3.0):
+        """Returns once the first sample has arrived (or after timeout_s)."""
+        end = time.monotonic() + timeout_s
+        while self.proc is not None and not self.samples and time.monotonic() < end:
+            time.sleep(0.01)
+
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out = ""
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            if self._reader is not None:
+                self._reader.join(timeout=5)
 
-    def summary(self):
+    def summary(self, window=None, timed=None):
+        """Median SM clock and the throttle reasons seen over the samples that
+        arrived inside `window` (all samples if None); `timed` counts the
+        samples inside the timed region itself."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        picked = [l for t, l in self.samples if window is None or window[0] <= t <= window[1]]
+        for l in picked:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -141,10 +163,11 @@ class ClockSampler:
             for nm, v in zip(names, f[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if timed is not None:
+            out["samples_in_timed_region"] = sum(1 for t, _ in self.samples if timed[0] <= t <= timed[1])
+        return out
 
 
 # ------------------------------------------------------------ cpu baseline
@@ -339,8 +362,19 @@ def run_ours(args):
     flush_l2 = 4 * n * (3 if vals64 else 2 if pairs else 1) * 2 < L2_BYTES
     flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev) if flush_l2 else None
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # The clock record: nvidia-smi samples every 200 ms, and a timed region of
+    # tens of milliseconds may hold none.  So the sampler starts first, and
+    # the same sort runs, untimed, for CLOCK_SETTLE_S before the timed steps;
+    # the summary takes the samples from that start to the end of the traced
+    # steps (all under this load) and counts those inside the timed region.
     with ClockSampler(local) as clocks:
+        clocks.wait_first()
+        load_t0 = time.monotonic()
+        while time.monotonic() < load_t0 + CLOCK_SETTLE_S:
+            step()
+            torch.cuda.synchronize()
         barrier()
+        timed_t0 = time.monotonic()
         if flush_l2:
             step_ms = 0.0
             for _ in range(args.steps):
@@ -356,12 +390,16 @@ def run_ours(args):
                 step()
             ev1.record(stream)
         barrier()
+        timed_t1 = time.monotonic()
         rs.rs_check_device_error()
         rs.rs_trace_enable(True)
         for _ in range(args.steps):
             step()
         barrier()
         rs.rs_trace_enable(False)
+        load_t1 = time.monotonic()
+    clock_summary = clocks.summary((load_t0, load_t1), (timed_t0, timed_t1))
+    clock_summary["settle_s"] = CLOCK_SETTLE_S
     rs.rs_check_device_error()
     trace = rs.rs_trace_read()
     ms = max_over_ranks(step_ms if flush_l2 else ev0.elapsed_time(ev1), world, dev)
@@ -407,7 +445,7 @@ def run_ours(args):
         waves = traffic_from_profiles("onesweep.cuh", key + "_smem_wavefronts")
         if waves:
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
-            csum = clocks.summary()
+            csum = clock_summary
             mhz = csum.get("sm_mhz") or csum.get("sm_max_mhz") or 2070.0
             per_cycle = waves / (avg_ms * 1e-3 * mhz * 1e6 * sms)
             roof["smem"] = {"wavefronts_per_launch": waves, "achieved_per_sm_cycle": per_cycle,
@@ -500,7 +538,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "kernel_ms": {k: v["total_ms"] / max(v["launches"], 1) for k, v in trace.items()},
-            "clocks": clocks.summary(),
+            "clocks": clock_summary,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
