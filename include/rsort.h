@@ -258,12 +258,15 @@ rs_status rs_sort_u32_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
  *
  * The caller still owns keys_in and keys_out (device, n keys each) and
  * h_part_offsets (host, num_parts + 1, may be NULL).  Scratch comes from a
- * fixed array of about 4.5 MiB inside the library's device memory, reserved
- * on every GPU that loads the library until the process exits; nothing is
- * allocated or freed by the call.  n above RS_NOALLOC_MAX_KEYS is rejected
- * with RS_ERR_INVALID before any work.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress), so make that first
- * call before any stream capture.  All calls on a device share the array:
+ * fixed array of about 4.5 MiB inside the library's device memory, held on
+ * every GPU that uses it until the process exits; nothing is allocated or
+ * freed by the call.  n above RS_NOALLOC_MAX_KEYS is rejected with
+ * RS_ERR_INVALID before any work.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); under CUDA's lazy module
+ * loading (the default) that lookup is also what loads the array onto the
+ * device, so the first call can still fail for lack of device memory.  Make
+ * that first call during set-up (n = 0 does the set-up and sorts nothing)
+ * and before any stream capture.  All calls on a device share the array:
  * calls whose work overlaps on the GPU (e.g. on two streams) race and must
  * be serialised by the caller.  Results are identical to rs_sort_u32's.   */
 rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, uint64_t n,
@@ -275,12 +278,15 @@ rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, uint6
 /* Message for the last error raised on the calling thread ("" if none). */
 const char* rs_last_error(void);
 
-/* Waits for `stream`, then reports and clears the device error word of the
- * current device: RS_ERR_TIMEOUT if a kernel's bounded wait (the
- * cross-tile lookback) gave up since the last check; RS_ERR_CUDA if the
- * stream failed or a kernel's output-index check fired (the write was
- * skipped); else RS_OK.  The error word is shared by all streams of the
- * device.                                                                   */
+/* After the work already enqueued on `stream`, takes and clears the device
+ * error word of the current device in one atomic step (a one-thread kernel
+ * on the stream), waits for the stream and reports what it took:
+ * RS_ERR_TIMEOUT if a kernel's bounded wait (the cross-tile lookback) gave
+ * up since the last check; RS_ERR_CUDA if the stream failed or a kernel's
+ * output-index check fired (the write was skipped); else RS_OK.  The error
+ * word is shared by all streams of the device: a bit raised by a kernel on
+ * another stream is reported by whichever check takes it first, and a bit
+ * raised after this check's take is kept for the next one.                 */
 rs_status rs_check_device_error(rs_stream_t stream);
 
 /* ---- tracing ------------------------------------------------------------ */

@@ -25,7 +25,7 @@ __all__ = [
     "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_version", "rs_trace_enable",
     "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS", "rs_selftest_wait_timeout",
     "rs_sort_u32_host", "rs_sort_u64", "sort64", "rs_sort_u64_pairs", "rs_sort_u64_pairs64", "sort64_pairs", "rs_sort_u32_pairs64", "sort_pairs64", "rs_merge_u32", "merge",
-    "sort", "sort_pairs", "sort_segmented", "temp_bytes", "part_offsets",
+    "sort", "sort_pairs", "sort_segmented", "temp_bytes",
     "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD", "RS_KEY_U32", "RS_KEY_I32", "RS_KEY_F32",
 ]
 
@@ -354,12 +354,6 @@ def rs_trace_read() -> dict:
 
 
 # --------------------------------------------------------------- conveniences
-def part_offsets(n: int, num_parts: int = 64) -> np.ndarray:
-    """Host copy of the partition offsets formula (no device work)."""
-    q, r = divmod(n, num_parts)
-    return np.array([p * q + min(p, r) for p in range(num_parts + 1)], dtype=np.uint64)
-
-
 def _empty_u32(n, device, like=None):
     """An output buffer of n 32-bit words (the input's dtype when given:
     int32 storage of uint32 keys, or float32 / int32 keys of another kind)."""

@@ -43,13 +43,21 @@ rs_status cuda_fail(cudaError_t e, const char* what) {
 
 // Device error word: set by kernels whose bounded waits gave up.
 __device__ uint32_t g_err_word;
+// Where take_error_kernel leaves the word it took (read back by the host).
+__device__ uint32_t g_err_taken;
+
+// Reads and clears the error word in one atomic step, so that a bit a kernel
+// on another stream sets in between is kept for the next check, not lost.
+__global__ void take_error_kernel(uint32_t* err, uint32_t* taken) { *taken = atomicExch(err, 0u); }
 
 struct DeviceState {
   bool ready = false;
   uint32_t* err = nullptr;
+  uint32_t* err_taken = nullptr;
   int num_sms = 0;
 };
 std::mutex g_mu;
+std::mutex g_err_mu;  // one error-word check at a time (they share the copy word)
 DeviceState g_dev[kMaxDevices];
 
 rs_status device_state(DeviceState** out) {
@@ -60,6 +68,8 @@ rs_status device_state(DeviceState** out) {
   DeviceState& st = g_dev[dev];
   if (!st.ready) {
     RS_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&st.err), g_err_word), "cudaGetSymbolAddress(error word)");
+    RS_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&st.err_taken), g_err_taken),
+            "cudaGetSymbolAddress(error word copy)");
     RS_CUDA(cudaDeviceGetAttribute(&st.num_sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     int cnt = 0;
     for (int r : {8, 11}) {
@@ -1301,12 +1311,18 @@ rs_status rs_check_device_error(rs_stream_t stream) {
   rs_status st = device_state(&ds);
   if (st != RS_OK) return st;
   const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  RS_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  // One thread takes the word (atomic exchange with zero) after the stream's
+  // earlier work; the host then reads what it took.  Serialised per device so
+  // that two checking threads do not share the copy word.
   uint32_t word = 0;
-  RS_CUDA(cudaMemcpy(&word, ds->err, sizeof(word), cudaMemcpyDeviceToHost), "read device error word");
+  {
+    std::lock_guard<std::mutex> lock(g_err_mu);
+    take_error_kernel<<<1, 1, 0, s>>>(ds->err, ds->err_taken);
+    RS_CUDA(cudaGetLastError(), "launch take_error");
+    RS_CUDA(cudaMemcpyAsync(&word, ds->err_taken, sizeof(word), cudaMemcpyDeviceToHost, s), "read device error word");
+    RS_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  }
   if (word) {
-    const uint32_t zero = 0;
-    RS_CUDA(cudaMemcpy(ds->err, &zero, sizeof(zero), cudaMemcpyHostToDevice), "clear device error word");
     if (word & kErrTimeout) return fail(RS_ERR_TIMEOUT, "a bounded device-side wait gave up (error word 0x%x)", word);
     return fail(RS_ERR_CUDA, "a device-side output index check fired (error word 0x%x)", word);
   }

@@ -9,8 +9,12 @@
 // synchronise the whole device) is not acceptable, and code that must not
 // be able to fail with out-of-memory once it has started.  For them this
 // entry point keeps its scratch in a fixed array that lives in the
-// library's own device memory: it is reserved when the library is loaded on
-// a GPU and held until the process exits.
+// library's own device memory and is held until the process exits.  With
+// CUDA's lazy module loading (the default), the module holding the array is
+// loaded, and the array reserved, by the first call on each device (its
+// cudaGetSymbolAddress); that first call can therefore still fail for lack
+// of device memory.  Callers that must not fail later make it during set-up:
+// a call with n = 0 does the set-up and sorts nothing.
 //
 // The array is sized for at most RS_NOALLOC_MAX_KEYS keys (about 4.5 MiB).
 // Every call on a device uses the same array, and the array keeps whatever

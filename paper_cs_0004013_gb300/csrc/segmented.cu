@@ -339,9 +339,8 @@ cudaError_t launch_local(const LocalArgs& a, unsigned grid, cudaStream_t s) {
 
 }  // namespace
 
-// Tiled passes over large segments: 8-bit digits, 512 x 16 tiles.
-// Tiled passes over large segments: 512 x 24 tiles for keys, 512 x 16 with
-// payloads (the plain sort's best shapes).
+// Tiled passes over large segments, 8-bit digits: 512 x 24 tiles for keys,
+// 512 x 22 for key+payload.
 constexpr int kSegThreads = 512, kSegItemsKeys = 24, kSegItemsPairs = 22;
 // Local sorts: tiny segments <= 256 x 16 keys, small ones <= 1024 x 16 keys.
 constexpr int kTinyThreads = 256, kSmallThreads = 1024, kLocalItems = 16;

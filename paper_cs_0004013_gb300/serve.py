@@ -19,6 +19,13 @@ PyTorch is used for device memory, pinned host memory, streams and events
 only; all sorting runs in librsort's kernels.  Each request's result does not
 depend on what it was batched with (the segmented sort treats every segment
 on its own), which ``tests/test_gpu_serve.py`` checks bit for bit.
+
+When a batch completes, the server takes the device error word (bounded
+waits that gave up, output-index checks that fired) on the batch's stream.
+The word is shared by every stream of the device, so an error cannot be
+pinned on one batch: the completed batch and every batch still in flight at
+that moment are marked failed (``Request.error``), and ``run`` returns with
+``failed`` counting them instead of reporting wrong results as served.
 """
 from __future__ import annotations
 
@@ -29,7 +36,7 @@ from collections import deque
 
 import numpy as np
 
-from . import rs_sort_u32, rs_sort_u32_host, rs_sort_u32_pairs, rs_sort_u32_segmented
+from . import RsError, rs_check_device_error, rs_sort_u32, rs_sort_u32_host, rs_sort_u32_pairs, rs_sort_u32_segmented
 
 __all__ = ["Request", "SortServer", "serial_plain", "latency_stats"]
 
@@ -48,6 +55,7 @@ class Request:
     out_vals: object = None
     done_s: float | None = None
     batch: int | None = None
+    error: str | None = None   # set when the device reported an error for the request's batch
 
     @staticmethod
     def make(rid: int, arrival_s: float, keys: np.ndarray, vals: np.ndarray | None = None) -> "Request":
@@ -133,6 +141,8 @@ class SortServer:
         self.next_batch = 0
         self.t0_event = None
         self.t0_host = None
+        self.suspect: dict[int, str] = {}  # batch id -> error seen while it was in flight
+        self.failed = 0
 
     # -- pinned staging buffers, reused by size class
     def _pinned(self, key, nbytes):
@@ -213,9 +223,25 @@ class SortServer:
         b.offs = offs
         self.in_flight.append(b)
 
+    def _check_errors(self, b):
+        """Takes the device error word after batch b's work; on an error, marks
+        b and every batch still in flight (any of them may have raised it)."""
+        try:
+            rs_check_device_error(b.stream)
+        except RsError as e:
+            msg = str(e)
+            self.suspect[b.id] = msg
+            for o in self.in_flight:
+                self.suspect.setdefault(o.id, msg)
+
     def _retire(self, b, now_s):
+        self._check_errors(b)
+        err = self.suspect.pop(b.id, None)
         for r in b.reqs:
             r.done_s = now_s
+            r.error = err
+            if err is not None:
+                self.failed += 1
         if b.arena is not None:
             self.pool.give(b.arena)
             self._return_pinned("off", b.h_in)
@@ -313,6 +339,7 @@ def serial_plain(requests: list[Request], num_parts: int = 64, device: str = "cu
 
 
 def latency_stats(requests: list[Request]) -> dict:
-    lat = np.array([r.done_s - r.arrival_s for r in requests])
+    """p50 / p99 / mean latency of the requests served without a device error."""
+    lat = np.array([r.done_s - r.arrival_s for r in requests if r.error is None])
     return {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
             "mean_ms": float(lat.mean() * 1e3)}

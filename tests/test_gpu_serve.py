@@ -90,3 +90,32 @@ def test_direct_and_batched_requests_mixed(realtime):
         else:
             wk = oracle.sort_keys(keys)
         assert np.array_equal(got_k, wk), r.id
+
+
+def test_device_error_marks_requests_failed():
+    """An error raised on the device while batches run (here the bounded-wait
+    self-test, which sets the error word without a fault) is not served as a
+    result: the batch that sees it, and every batch in flight with it, are
+    marked failed; the run after that is clean."""
+    import torch
+    import paper_cs_0004013_gb300 as rs
+    from paper_cs_0004013_gb300.serve import SortServer, latency_stats
+    rs.rs_check_device_error()
+    temp = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    rs.rs_selftest_wait_timeout(temp)
+    torch.cuda.synchronize()
+    reqs = _requests(10, 13, rate=1e6)
+    srv = SortServer(slots=2, streams=2, mem_budget=1 << 30)
+    srv.run(reqs, realtime=False)
+    assert srv.failed >= 1
+    assert srv.failed == sum(r.error is not None for r in reqs)
+    assert all("TIMEOUT" in r.error for r in reqs if r.error is not None)
+    rs.rs_check_device_error()  # taken by the server: the word is clear
+    reqs2 = _requests(10, 14, rate=1e6)
+    srv2 = SortServer(slots=2, streams=2, mem_budget=1 << 30)
+    srv2.run(reqs2, realtime=False)
+    assert srv2.failed == 0 and all(r.error is None for r in reqs2)
+    for r in reqs2:
+        got_k, _ = r.result()
+        assert np.array_equal(got_k, oracle.sort_keys(r.keys.numpy().view(np.uint32)))
+    assert latency_stats(reqs2)["p50_ms"] > 0

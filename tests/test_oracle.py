@@ -246,11 +246,27 @@ def test_distribute_bruteforce_and_lsd_theorem():
         assert np.array_equal(k, sk) and np.array_equal(v, sv), bits
 
 
-def test_msd_buckets_then_local_sort():
-    keys = synth.tight_clusters(5000, 3)
+def check_msd_offsets(keys, k, offs, shift, width):
+    """Bucket b of the bucketing phase (Sec. 3.2) holds exactly the keys whose
+    top digit is b: its size is the brute-force count of that digit, and every
+    key inside its range carries that digit."""
+    counts = brute_histogram(keys, shift, width)
+    assert offs.size == (1 << width) + 1 and int(offs[0]) == 0
+    for b in range(1 << width):
+        a, e = int(offs[b]), int(offs[b + 1])
+        assert e - a == counts[b], b
+        assert all(((int(x) >> shift) & ((1 << width) - 1)) == b for x in k[a:e]), b
+
+
+@pytest.mark.parametrize("dist,n,shift,width", [
+    ("tight_clusters", 5000, 21, 11), ("uniform31", 3000, 18, 13), ("few_distinct", 2000, 20, 12),
+])
+def test_msd_buckets_then_local_sort(dist, n, shift, width):
+    keys = getattr(synth, dist)(n, 3)
     vals = np.arange(keys.size, dtype=np.uint32)
-    k, v, offs = oracle.msd_buckets(keys, vals, 21, 11)
+    k, v, offs = oracle.msd_buckets(keys, vals, shift, width)
     assert int(offs[0]) == 0 and int(offs[-1]) == keys.size
+    check_msd_offsets(keys, k, offs, shift, width)
     # sorting each bucket on its own gives the full stable sort
     outk, outv = k.copy(), v.copy()
     for b in range(offs.size - 1):
@@ -258,6 +274,20 @@ def test_msd_buckets_then_local_sort():
         outk[a:e], outv[a:e] = oracle.sort_pairs(k[a:e], v[a:e])
     sk, sv = oracle.sort_pairs(keys, vals)
     assert np.array_equal(outk, sk) and np.array_equal(outv, sv)
+
+
+def test_msd_offsets_pin_catches_shifted_bases():
+    """A plausible mistake: the bucket offsets taken as the exclusive bases
+    shifted by one slot.  On clustered keys the top bucket is empty, so the
+    last offset still equals n; the per-bucket check must still fail."""
+    keys = synth.tight_clusters(5000, 3)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    k, _, offs = oracle.msd_buckets(keys, vals, 21, 11)
+    wrong = np.zeros_like(offs)
+    wrong[1:] = oracle.digit_bases(oracle.digit_histograms(keys, [(21, 11)])[0])
+    assert int(wrong[0]) == 0 and int(wrong[-1]) == keys.size  # the ends alone do not see it
+    with pytest.raises(AssertionError):
+        check_msd_offsets(keys, k, wrong, 21, 11)
 
 
 def test_skippable_digits():

@@ -40,6 +40,26 @@ def test_noalloc_matches_regular_entry_point_on_back_to_back_calls(rs):
             assert np.array_equal(offs, want_offs), n
 
 
+def test_noalloc_calls_allocate_no_device_memory(rs):
+    """The property the entry point exists for: once the first call on the
+    device has set it up, further calls change neither PyTorch's allocation
+    count nor the device's free memory."""
+    import torch
+    n = rs.RS_NOALLOC_MAX_KEYS
+    d = to_dev(synth.uniform31(n, 9200))
+    got = torch.empty_like(d)
+    rs.rs_sort_u32_noalloc(d, got, 0, 64)  # set-up only
+    rs.rs_sort_u32_noalloc(d, got, n, 64)  # warm-up: every kernel the sort uses is loaded
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    for _ in range(4):
+        rs.rs_sort_u32_noalloc(d, got, n, 64)
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_rejects_more_keys_than_its_scratch_holds(rs):
     with pytest.raises(rs.RsError) as e:
         rs.rs_sort_u32_noalloc(None, None, rs.RS_NOALLOC_MAX_KEYS + 1, 64)
