@@ -258,13 +258,25 @@ def whole_job_rate(keys_per_rank: int, world: int, steps: int, job_ms: float) ->
 
 
 # ------------------------------------------------------------------ ours
-def traffic_from_profiles(kernel_file: str, key: str):
+PASS_SOURCES = ("onesweep.cuh", "onesweep2.cuh", "onesweep_r8.cu")
+
+
+def pass_kernel_sha() -> str:
+    """First 16 hex digits of the sha256 of the 8-bit pass kernels' sources
+    (both kernel forms and the tile-shape registry that picks between them)."""
+    h = hashlib.sha256()
+    for f in PASS_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_cs_0004013_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profiles(key: str):
     """DRAM bytes per launch recorded by ncu for the pass kernel, valid only
-    while the kernel source is unchanged (its sha256 is stored with it)."""
+    while the pass kernels' sources are unchanged (their sha256 is stored
+    with the figure)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    src = os.path.join(ROOT, "paper_cs_0004013_gb300", "csrc", kernel_file)
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        sha = pass_kernel_sha()
         for line in open(path):
             f = line.split()
             if len(f) >= 3 and f[0] == key and f[1] == sha:
@@ -435,14 +447,14 @@ def run_ours(args):
         achieved = bytes_launch / (avg_ms * 1e-3) / 1e9
         key = (f"{pass_kind}_{('keys64v64' if wide_v64 else 'keys64') if wide else ('pairs64' if vals64 else 'pairs' if pairs else 'keys')}"
                f"_n{n}")
-        traffic = traffic_from_profiles("onesweep.cuh", key)
+        traffic = traffic_from_profiles(key)
         roof = {"bound": "hbm", "kernel": pass_kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_ms}
         # The resource that binds the pass: shared-memory wavefronts (one per SM
         # per cycle at most).  Wavefronts per launch come from the same ncu
         # capture as the traffic; the rate uses this run's launch time and SM clock.
-        waves = traffic_from_profiles("onesweep.cuh", key + "_smem_wavefronts")
+        waves = traffic_from_profiles(key + "_smem_wavefronts")
         if waves:
             sms = torch.cuda.get_device_properties(dev).multi_processor_count
             csum = clock_summary

@@ -174,10 +174,12 @@ struct SortPlan {
 // (shape 0) below that and for pairs (which need twice the staging memory).
 int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 8; }
 uint32_t default_mode(uint64_t /*n*/, bool /*pairs*/) { return RS_MODE_LSD; }
-// 512 x 24 tiles for keys and for key+payload sorts (GB300, 2^26 keys: 260 and
-// 342 us per pass against 296 and 351 with 512 x 16); 512 x 16 up to 2^22 keys.
+// Above 2^22 keys: the half-warp-group kernel at 384 x 24 for keys (GB300,
+// 2^26 keys: 233 us per pass against 260 with the lane-mask kernel at
+// 512 x 24) and the lane-mask kernel at 512 x 24 for key+payload sorts (343
+// us against 385 for the half-warp-group kernel); 512 x 16 up to 2^22 keys.
 uint32_t default_tile(int R, bool pairs, uint64_t n) {
-  if (R == 8) return n <= (uint64_t(1) << 22) ? 1u : 3u;
+  if (R == 8) return n <= (uint64_t(1) << 22) ? 1u : (pairs ? 3u : 2u);
   return pairs ? 1u : 4u;
 }
 
@@ -250,8 +252,8 @@ rs_status make_plan(uint64_t n, bool pairs, const rs_plan* user, SortPlan* p, in
   }
   const bool wide = needs_wide_status(n);
   uint32_t tile = (user && user->tile) ? user->tile : default_tile(p->R, pairs, n);
-  // 64-bit status kernels: shape 0 (keys and pairs) and shape 2 (keys)
-  if (wide && !(user && user->tile)) tile = (pairs || p->R != 8) ? 1u : 3u;
+  // 64-bit status kernels: shapes 0, 1 and 4 (keys and pairs), shape 2 (keys)
+  if (wide && !(user && user->tile)) tile = (pairs || p->R != 8) ? 1u : 2u;
   rs_status st = pick_kernel(p->R, tile, vwords >= 0 ? vwords : (pairs ? 1 : 0), wide, &p->k);
   if (st != RS_OK) return st;
   p->num_tiles = (n + p->k->tile - 1) / p->k->tile;

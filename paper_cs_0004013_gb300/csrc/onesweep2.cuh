@@ -1,0 +1,326 @@
+// The LSD distribution pass by an 8-bit digit with half-warp rank groups and
+// early digit counts ("onesweep", second form).
+//
+// Paper: the same step as onesweep.cuh, the bucketing/distribution of
+// Sec. 3.2 (count per bucket, cumulative totals, the partial sort grouping
+// keys by bucket in ascending order, distribution of contiguous bucket
+// ranges) done exactly, stable so that the repeated low-to-high passes sort
+// (Sec. 3.3.1).  What differs is how a tile ranks its keys:
+//
+//  * Rank groups are half-warps.  Group g (warp w, half h) owns a contiguous
+//    run of 16 * ITEMS keys of the tile: item j of its lane l is the run's
+//    key j * 16 + l, so the group's keys in (item, lane) order are in input
+//    order, and the groups' runs follow each other in input order.
+//  * Early counts: every key first adds one to its group's counter for its
+//    digit (a shared-memory reduction, no return value).  The tile's count
+//    per digit is then known before any key is ranked: it is published as
+//    the tile's aggregate status at once (so that successors' lookbacks
+//    rarely wait), the digit threads scan it, and each (group, digit)
+//    counter is replaced by the position, in the digit-sorted tile, of the
+//    group's first key with that digit.
+//  * One 32-bit word per (group, digit) holds [lane mask : 16 | position :
+//    16].  Per item, each lane ORs its bit into the mask of its digit, reads
+//    the word back (the lanes of its group with the same digit, and where
+//    the run of that digit continues), and the highest such lane writes the
+//    advanced position with the mask cleared: three shared-memory accesses
+//    per key, after which the key's place in the staged tile is final and
+//    it is staged right away.
+//  * The digit threads (one per digit) run the lookback over earlier tiles
+//    before ranking their own keys, so its latency overlaps the other
+//    warps' ranking.
+//
+// Per tile (TILE = THREADS * ITEMS keys, tiles handed out by an atomic
+// ticket so that every predecessor of a tile is already running):
+//  1. load, 2. early counts, 3. per digit: aggregate status, scan, group
+//  positions, 4. lookback (digit threads) and rank + stage (all), 5. stage
+//  payloads (key+payload), 6. write out in tile order, each key to
+//  base[digit] + (keys of the digit in earlier tiles) + (position within
+//  the digit here).
+#pragma once
+
+#include "onesweep.cuh"
+
+namespace rs {
+
+template <int THREADS, int ITEMS, int NV>
+struct Onesweep2Layout {
+  static constexpr int DIGITS = 256;
+  static constexpr int WARPS = THREADS / 32;
+  static constexpr int GROUPS = 2 * WARPS;    // half-warp rank groups
+  static constexpr int TILE = THREADS * ITEMS;
+  static constexpr int GKEYS = 16 * ITEMS;    // keys of one group
+  static constexpr size_t KBUF = size_t(TILE) * 4;                 // staged keys
+  static constexpr size_t TBL = size_t(GROUPS) * DIGITS * 4;       // [GROUPS][DIGITS] rank words
+  // The rank words sit after the staged keys; with a payload they share
+  // their space with the staged payloads, which are written only after the
+  // last rank word is read.
+  static constexpr size_t OFF_TBL = KBUF;
+  static constexpr size_t END = (KBUF + TBL > KBUF * (1 + NV) ? KBUF + TBL : KBUF * (1 + NV));
+  static constexpr size_t OFF_GOFF = (END + 15) / 16 * 16;
+  static constexpr size_t OFF_SCAN = OFF_GOFF + size_t(DIGITS) * 4;
+  static constexpr size_t OFF_TILE = OFF_SCAN + 32 * 4;
+  static constexpr size_t SMEM = OFF_TILE + 16;
+  static_assert(THREADS % 32 == 0 && THREADS >= DIGITS && THREADS <= 1024, "one thread per digit at least");
+  static_assert(TILE < 65536, "positions are 16-bit");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+// 32-bit shared-memory accesses by address (the hot loop's tables).
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void sh_red_add(uint32_t a, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void sh_red_or(uint32_t a, uint32_t v) {
+  asm volatile("red.shared.or.b32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t sh_ld(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sh_st(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_global(uint32_t* p, uint32_t v) {
+  asm volatile("st.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Byte `sel & 3` of k as the low byte of the result (a byte permute with the
+// upper three bytes taken from zero): the 8-bit digit at shift 8 * (sel & 3).
+__device__ __forceinline__ uint32_t byte_digit(uint32_t k, uint32_t sel) { return __byte_perm(k, 0u, sel); }
+
+// Exclusive prefix sum over the first 256 threads of the block (8 warps),
+// synchronised by named barrier 1; s_scan holds 8 words.
+__device__ __forceinline__ uint32_t scan256_exclusive(uint32_t x, uint32_t* s_scan) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_scan[w] = inc;
+  asm volatile("bar.sync 1, 256;" ::: "memory");
+  uint32_t before = 0;
+#pragma unroll
+  for (int i = 0; i < 7; ++i)
+    if (i < w) before += s_scan[i];
+  return before + inc - x;
+}
+
+template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB>
+__global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs a) {
+  using L = Onesweep2Layout<THREADS, ITEMS, NV>;
+  constexpr int DIGITS = L::DIGITS, GROUPS = L::GROUPS, TILE = L::TILE;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Route route = route_of(a.skip, a.pass, a.num_passes);
+  if (!route.active) return;
+  const uint32_t* kin = route.src == BUF_IN ? a.keys_in : (route.src == BUF_OUT ? a.keys_out : a.keys_alt);
+  uint32_t* kout = route.dst == BUF_OUT ? a.keys_out : a.keys_alt;
+  const uint32_t* vin = nullptr;
+  uint32_t* vout = nullptr;
+  if constexpr (NV >= 1) {
+    vin = route.src == BUF_IN ? a.vals_in : (route.src == BUF_OUT ? a.vals_out : a.vals_alt);
+    vout = route.dst == BUF_OUT ? a.vals_out : a.vals_alt;
+  }
+  const KeyXform xin = route.src == BUF_IN ? a.xin : KeyXform{0u, 0u};
+  const KeyXform xout = route.last ? a.xout : KeyXform{0u, 0u};
+  const uint32_t parity = route.parity;
+  S* status = reinterpret_cast<S*>(a.status);
+
+  uint32_t* s_key = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* s_val = reinterpret_cast<uint32_t*>(smem + L::KBUF);
+  uint32_t* s_tbl = reinterpret_cast<uint32_t*>(smem + L::OFF_TBL);
+  uint32_t* s_goff = reinterpret_cast<uint32_t*>(smem + L::OFF_GOFF);
+  uint32_t* s_scan = reinterpret_cast<uint32_t*>(smem + L::OFF_SCAN);
+  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int l16 = lane & 15, grp = warp * 2 + (lane >> 4);
+
+  // 0. clear the rank words, take the tile ticket
+  {
+    uint4* t4 = reinterpret_cast<uint4*>(s_tbl);
+#pragma unroll 4
+    for (int i = tid; i < int(L::TBL / 16); i += THREADS) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) *s_tile = atomicAdd(a.tile_counter, 1u);
+  }
+  __syncthreads();
+  const uint32_t tile = *s_tile;
+  const size_t tbase = size_t(tile) * TILE;
+  const size_t left = size_t(a.n) - tbase;
+  const uint32_t valid = left < size_t(TILE) ? uint32_t(left) : uint32_t(TILE);
+  const uint32_t sel = 0x4440u | (a.shift >> 3);
+
+  // 1. load: group grp takes keys [grp * GKEYS, (grp + 1) * GKEYS) of the
+  // tile, item j of lane l16 being key grp * GKEYS + j * 16 + l16.  Keys
+  // past the end act as 0xFFFFFFFF: their digit is the largest and they
+  // come after every real key, so they sort to the tile's tail and are
+  // never written.
+  uint32_t key[ITEMS];
+  const uint32_t goff_in = uint32_t(grp) * L::GKEYS + uint32_t(l16);
+  if (valid == TILE) {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) key[j] = ld_stream(kin + tbase + goff_in + j * 16);
+    if (!is_identity(xin)) {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) key[j] = to_ordered(key[j], xin);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t i = goff_in + j * 16;
+      key[j] = i < valid ? to_ordered(kin[tbase + i], xin) : 0xffffffffu;
+    }
+  }
+
+  // 2. early counts per (group, digit)
+  const uint32_t tb_grp = smem_addr(s_tbl + grp * DIGITS);
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) sh_red_add(tb_grp + 4u * byte_digit(key[j], sel), 1u);
+  __syncthreads();
+
+  // 3. per digit (threads 0..255): the tile's count -> aggregate status now;
+  // exclusive scan over digits -> where each digit's run starts in the
+  // staged tile; then each group's counter -> the position of its first key
+  // of the digit
+  uint32_t tot = 0, excl = 0;
+  if (tid < DIGITS) {
+#pragma unroll 8
+    for (int g = 0; g < GROUPS; ++g) tot += s_tbl[g * DIGITS + tid];
+    st_relaxed(status + size_t(tile) * DIGITS + tid, status_word<S>(parity, tile == 0, tot));
+    excl = scan256_exclusive(tot, s_scan);
+    uint32_t run = excl;
+#pragma unroll 8
+    for (int g = 0; g < GROUPS; ++g) {
+      const uint32_t c = s_tbl[g * DIGITS + tid];
+      s_tbl[g * DIGITS + tid] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+
+  // 4a. lookback over earlier tiles (digit threads): publishes this tile's
+  // inclusive counts and the digit's output offset for the write-out.  Run
+  // before the digit threads rank their own keys (EARLY_LB), it overlaps the
+  // other warps' ranking; after, it needs fewer live registers.
+  auto do_lookback = [&]() {
+    if (tid < DIGITS) {
+      uint32_t prefix[1];
+      lookback<DIGITS, 1, S, LB>(status, tile, 0u, tid, parity, a.err, prefix);
+      if (tile != 0) st_relaxed(status + size_t(tile) * DIGITS + tid, status_word<S>(parity, true, prefix[0] + tot));
+      s_goff[tid] = a.bases[tid] + prefix[0] - excl;
+    }
+  };
+  if constexpr (EARLY_LB) do_lookback();
+
+  // 4b. rank within the group and stage the key at its final tile position
+  const uint32_t lt16 = (1u << l16) - 1u;
+  const uint32_t mybit = 1u << (16 + l16);
+  const uint32_t sk = smem_addr(s_key);
+  uint32_t pos[NV >= 1 ? (ITEMS + 1) / 2 : 1];
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const uint32_t ad = tb_grp + 4u * byte_digit(key[j], sel);
+    sh_red_or(ad, mybit);
+    __syncwarp();
+    const uint32_t v = sh_ld(ad);
+    const uint32_t peers = v >> 16, base = v & 0xffffu;
+    const uint32_t p = base + __popc(peers & lt16);
+    if ((peers >> l16) == 1u) sh_st(ad, base + __popc(peers));  // the group's highest lane with this digit
+    __syncwarp();
+    sh_st(sk + 4u * p, key[j]);
+    if constexpr (NV >= 1) {
+      if (j & 1) pos[j >> 1] |= p << 16;
+      else pos[j >> 1] = p;
+    }
+  }
+  if constexpr (!EARLY_LB) do_lookback();
+  __syncthreads();
+
+  // 5. payloads: staged at their keys' positions (over the dead rank words)
+  if constexpr (NV >= 1) {
+    uint32_t val[ITEMS];
+    if (valid == TILE) {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(vin + tbase + goff_in + j * 16);
+    } else {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t i = goff_in + j * 16;
+        val[j] = i < valid ? vin[tbase + i] : 0u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) s_val[(pos[j >> 1] >> (16 * (j & 1))) & 0xffffu] = val[j];
+    __syncthreads();
+  }
+
+  // 6. write out in tile order: runs of one digit go to consecutive
+  // addresses.  Keys are read from shared memory and their offsets looked up
+  // a batch at a time before the batch's stores, so that the stores (global,
+  // through an explicit global-space instruction) do not serialise the
+  // shared-memory loads behind them (GB300, 2^26 keys: the write-out of a
+  // 512 x 24 tile went from about 8,300 to 5,100 SM cycles).  The range
+  // check only guards against a corrupted offset (it raises an error bit
+  // instead of writing out of bounds).
+  bool oob = false;
+  const uint32_t n = a.n;
+  const uint32_t sg = smem_addr(s_goff);
+  auto write_out = [&](auto invert) {
+    constexpr int B = ITEMS % 8 == 0 ? 8 : (ITEMS % 6 == 0 ? 6 : (ITEMS % 4 == 0 ? 4 : 1));
+#pragma unroll
+    for (int k0 = 0; k0 < ITEMS; k0 += B) {
+      uint32_t kk[B], g[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) kk[b] = sh_ld(sk + 4u * ((k0 + b) * THREADS + tid));
+#pragma unroll
+      for (int b = 0; b < B; ++b) g[b] = sh_ld(sg + 4u * byte_digit(kk[b], sel)) + (k0 + b) * THREADS + tid;
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const uint32_t i = (k0 + b) * THREADS + tid;
+        if (valid == TILE || i < valid) {
+          if (g[b] < n) {
+            st_global(kout + g[b], decltype(invert)::value ? from_ordered(kk[b], xout) : kk[b]);
+            if constexpr (NV >= 1) st_global(vout + g[b], sh_ld(smem_addr(s_val) + 4u * i));
+          } else {
+            oob = true;
+          }
+        }
+      }
+    }
+  };
+  if (is_identity(xout)) write_out(std::false_type{});
+  else write_out(std::true_type{});
+  if (oob) atomicOr(a.err, kErrBounds);
+}
+
+template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB>
+cudaError_t launch_onesweep2(const PassArgs& a, unsigned grid, cudaStream_t s) {
+  using L = Onesweep2Layout<THREADS, ITEMS, NV>;
+  onesweep2_kernel<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB><<<grid, THREADS, L::SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+// EARLY_LB: the digit threads run the lookback before ranking their keys;
+// LB: predecessors' status words a digit thread reads per lookback round.
+template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB = false, int LB = 8>
+OnesweepKernel make_onesweep2(int shape_id) {
+  using L = Onesweep2Layout<THREADS, ITEMS, NV>;
+  return OnesweepKernel{8,
+                        shape_id,
+                        THREADS,
+                        ITEMS,
+                        L::TILE,
+                        NV >= 1,
+                        sizeof(S) == 8,
+                        L::SMEM,
+                        &launch_onesweep2<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB>,
+                        reinterpret_cast<const void*>(&onesweep2_kernel<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB>),
+                        0,
+                        NV,
+                        false};
+}
+
+}  // namespace rs

@@ -1,38 +1,41 @@
 // Onesweep pass kernels with 8-bit digits (four passes over 32-bit keys).
 #include "onesweep.cuh"
-#include "onesweep_pipe.cuh"
+#include "onesweep2.cuh"
 
 namespace rs {
 
 using S32 = uint32_t;
 using S64 = unsigned long long;
 
-// Shape 0 is the default.  MINB = resident blocks per SM the register budget
-// is sized for; the last flag puts the lookback before the staging step.
+// Tile shapes (rs_plan.tile = shape + 1).  MINB = resident blocks per SM the
+// register budget is sized for.
+//   0: 512 x 16, lane-mask tables (onesweep.cuh): every payload layout, 64-bit
+//      status words, the interleaved 64-bit reads and writes;
+//   1: 384 x 24, half-warp rank groups (onesweep2.cuh), three blocks per SM:
+//      the keys-only default above 2^22 keys;
+//   2: 512 x 24, lane-mask tables: the key+payload default above 2^22 keys;
+//   3: 1024 x 16, lane-mask tables, one block per SM;
+//   4-6: half-warp rank groups at 512 x 24, 512 x 16 and 256 x 24.
+// GB300, 2^26 uniform 31-bit keys, per pass: shape 1 233 us (keys), shape 2
+// 260 us (keys) and 343 us (key+payload), shape 4 238 / 385 us.
 static const OnesweepKernel kR8[] = {
     make_onesweep<8, 512, 16, false, S32, 2, false>(0), make_onesweep<8, 512, 16, true, S32, 2, false>(0),
     make_onesweep<8, 512, 16, false, S64, 2, false>(0), make_onesweep<8, 512, 16, true, S64, 2, false>(0),
     // two payload words (64-bit keys with a value: the other key word and the value),
     // with the interleaved 64-bit reads and writes of the 64-bit sorts
     make_onesweep<8, 512, 16, 2, S32, 2, false, true>(0), make_onesweep<8, 512, 16, 2, S64, 2, false, true>(0),
-    // the interleaved variants of the default key+payload kernel (64-bit keys)
+    // the interleaved variants of the key+payload kernel (64-bit keys)
     make_onesweep<8, 512, 16, true, S32, 2, false, true>(0), make_onesweep<8, 512, 16, true, S64, 2, false, true>(0),
-    make_onesweep<8, 512, 16, false, S32, 2, true>(1),  make_onesweep<8, 512, 16, true, S32, 2, true>(1),
+    make_onesweep2<384, 24, 0, S32, 3>(1), make_onesweep2<384, 24, 1, S32, 3>(1),
+    make_onesweep2<384, 24, 0, S64, 3>(1), make_onesweep2<384, 24, 1, S64, 3>(1),
     make_onesweep<8, 512, 24, false, S32, 2, false>(2), make_onesweep<8, 512, 24, true, S32, 2, false>(2),
     make_onesweep<8, 512, 24, false, S64, 2, false>(2),
     make_onesweep<8, 512, 24, true, S32, 2, false, true>(2),  // interleaved: 64-bit keys
     make_onesweep<8, 1024, 16, false, S32, 1, false>(3), make_onesweep<8, 1024, 16, true, S32, 1, false>(3),
-    make_onesweep<8, 384, 20, false, S32, 2, false>(4), make_onesweep<8, 384, 20, true, S32, 2, false>(4),
-    // persistent, software-pipelined (onesweep_pipe.cuh)
-    make_onesweep_pipe<8, 512, 16, false, S32, 2>(5),   make_onesweep_pipe<8, 512, 16, true, S32, 1>(5),
-    make_onesweep_pipe<8, 256, 24, false, S32, 3>(6),   make_onesweep_pipe<8, 256, 24, true, S32, 2>(6),
-    make_onesweep_pipe<8, 384, 20, false, S32, 2>(7),   make_onesweep_pipe<8, 384, 20, true, S32, 1>(7),
-    make_onesweep_pipe<8, 512, 24, false, S32, 1>(8),   make_onesweep_pipe<8, 512, 24, true, S32, 1>(8),
-    make_onesweep_pipe<8, 256, 16, false, S32, 4>(9),   make_onesweep_pipe<8, 256, 16, true, S32, 2>(9),
-    // smaller blocks, more of them per SM
-    make_onesweep<8, 256, 24, false, S32, 4, false>(10), make_onesweep<8, 256, 24, true, S32, 3, false>(10),
-    make_onesweep<8, 256, 32, false, S32, 3, false>(11), make_onesweep<8, 256, 32, true, S32, 2, false>(11),
-    make_onesweep<8, 384, 24, false, S32, 2, false>(12), make_onesweep<8, 384, 24, true, S32, 2, false>(12),
+    make_onesweep2<512, 24, 0, S32, 2>(4), make_onesweep2<512, 24, 1, S32, 2>(4),
+    make_onesweep2<512, 24, 0, S64, 2>(4), make_onesweep2<512, 24, 1, S64, 2>(4),
+    make_onesweep2<512, 16, 0, S32, 2>(5), make_onesweep2<512, 16, 1, S32, 2>(5),
+    make_onesweep2<256, 24, 0, S32, 4>(6), make_onesweep2<256, 24, 1, S32, 4>(6),
 };
 
 const OnesweepKernel* onesweep_kernels_r8(int* count) {

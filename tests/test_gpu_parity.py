@@ -127,7 +127,7 @@ def test_sort_edge_values(rs, kind):
         _pairs_check(rs, keys, plan={"digit_bits": bits})
 
 
-@pytest.mark.parametrize("tile", list(range(1, 14)))
+@pytest.mark.parametrize("tile", list(range(1, 8)))
 @pytest.mark.parametrize("bits", [8, 11])
 def test_tile_shapes(rs, tile, bits):
     """Every registered tile shape (plain and persistent pipelined kernels),
