@@ -38,7 +38,7 @@ import numpy as np
 
 from . import RsError, rs_check_device_error, rs_sort_u32, rs_sort_u32_host, rs_sort_u32_pairs, rs_sort_u32_segmented
 
-__all__ = ["Request", "SortServer", "serial_plain", "latency_stats"]
+__all__ = ["Request", "ResultPool", "SortServer", "serial_plain", "latency_stats"]
 
 
 @dataclasses.dataclass
@@ -46,7 +46,8 @@ class Request:
     """One sort request.  keys / vals are pinned host tensors (int32 storage
     of uint32 values) owned by the client; the server copies them to the
     device and the sorted result back into out_keys / out_vals (pinned,
-    allocated with the request), with no host-side copy in between."""
+    allocated with the request, or lent by the server's ResultPool until
+    on_done returns), with no host-side copy in between."""
     id: int
     arrival_s: float           # offset from the start of the run
     keys: object               # pinned torch.int32 [n]
@@ -56,6 +57,7 @@ class Request:
     done_s: float | None = None
     batch: int | None = None
     error: str | None = None   # set when the device reported an error for the request's batch
+    pooled: object = dataclasses.field(default=None, repr=False)  # result buffers lent by a ResultPool
 
     @staticmethod
     def make(rid: int, arrival_s: float, keys: np.ndarray, vals: np.ndarray | None = None) -> "Request":
@@ -66,6 +68,13 @@ class Request:
         r.out_keys = torch.empty_like(k).pin_memory()
         r.out_vals = None if v is None else torch.empty_like(v).pin_memory()
         return r
+
+    @staticmethod
+    def view(rid: int, arrival_s: float, keys, vals=None) -> "Request":
+        """A request over pinned int32 tensors the client already holds (for
+        example slices of one pinned pool).  Its result buffers are left
+        unset: a server with a result pool hands them out at admission."""
+        return Request(rid, arrival_s, keys, vals)
 
     @property
     def n(self) -> int:
@@ -109,6 +118,33 @@ class _Pool:
         self.free.setdefault(buf.numel(), []).append(buf)
 
 
+class ResultPool:
+    """Pinned host buffers for results, reused by size class, with a cap on
+    the bytes handed out at once.  A server given one assigns result buffers
+    to requests that have none when it admits them (admission waits while
+    the cap is reached), calls the client's on_done(request) when a request
+    completes, and then takes its buffers back: the client reads or copies
+    the result inside on_done."""
+
+    def __init__(self, max_bytes: int):
+        self.max_bytes = max_bytes
+        self.out = 0
+        self.free: dict[int, list] = {}
+
+    def take(self, nbytes: int):
+        import torch
+        c = _size_class(nbytes)
+        if self.out + c > self.max_bytes and self.out > 0:
+            return None
+        self.out += c
+        lst = self.free.get(c)
+        return lst.pop() if lst else torch.empty(c, dtype=torch.uint8).pin_memory()
+
+    def give(self, buf):
+        self.out -= buf.numel()
+        self.free.setdefault(buf.numel(), []).append(buf)
+
+
 class _Batch:
     def __init__(self, bid, reqs, pairs, stream, arena, temp, h_in, h_out, done_event, start_event):
         self.id, self.reqs, self.pairs, self.stream = bid, reqs, pairs, stream
@@ -127,8 +163,9 @@ class SortServer:
 
     def __init__(self, slots: int = 8, streams: int = 8, mem_budget: int = 8 << 30,
                  max_batch_keys: int = 1 << 24, num_parts: int = 64, device: str = "cuda",
-                 direct_min_keys: int = 1 << 22):
+                 direct_min_keys: int = 1 << 22, result_pool: ResultPool | None = None, on_done=None):
         import torch
+        self.result_pool, self.on_done = result_pool, on_done
         self.device = torch.device(device)
         self.slots, self.mem_budget, self.max_batch_keys = slots, mem_budget, max_batch_keys
         self.direct_min_keys = direct_min_keys
@@ -234,6 +271,26 @@ class SortServer:
             for o in self.in_flight:
                 self.suspect.setdefault(o.id, msg)
 
+    def _assign_results(self, r) -> bool:
+        """Gives r result buffers from the pool if it has none; False if the
+        pool is at its cap (r waits)."""
+        if r.out_keys is not None or self.result_pool is None:
+            return True
+        kb = self.result_pool.take(r.n * 4)
+        if kb is None:
+            return False
+        vb = None
+        if r.pairs:
+            vb = self.result_pool.take(r.n * 4)
+            if vb is None:
+                self.result_pool.give(kb)
+                return False
+        import torch
+        r.pooled = (kb, vb)
+        r.out_keys = kb[: r.n * 4].view(torch.int32)
+        r.out_vals = None if vb is None else vb[: r.n * 4].view(torch.int32)
+        return True
+
     def _retire(self, b, now_s):
         self._check_errors(b)
         err = self.suspect.pop(b.id, None)
@@ -242,6 +299,14 @@ class SortServer:
             r.error = err
             if err is not None:
                 self.failed += 1
+            if self.on_done is not None:
+                self.on_done(r)
+            if r.pooled is not None:
+                for buf in r.pooled:
+                    if buf is not None:
+                        self.result_pool.give(buf)
+                r.pooled = None
+                r.out_keys = r.out_vals = None
         if b.arena is not None:
             self.pool.give(b.arena)
             self._return_pinned("off", b.h_in)
@@ -287,6 +352,8 @@ class SortServer:
                     cost = 3 * r.bytes_needed()
                     if cost > budget and (group[False] or group[True] or self.in_flight):
                         break
+                    if not self._assign_results(r):
+                        break  # the result pool is at its cap: wait for completions
                     group[r.pairs].append(pending.popleft())
                     keys_in_batch[r.pairs] += r.n
                     budget -= cost
@@ -322,18 +389,23 @@ def serial_plain(requests: list[Request], num_parts: int = 64, device: str = "cu
     temp = torch.empty(max(rs_sort_u32_pairs(None, None, None, None, big), rs_sort_u32(None, None, big)),
                        dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # requests without result buffers of their own share one pinned scratch pair
+    need_scratch = any(r.out_keys is None for r in requests)
+    sk = torch.empty(big, dtype=torch.int32).pin_memory() if need_scratch else None
+    sv = torch.empty(big, dtype=torch.int32).pin_memory() if need_scratch else None
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for r in requests:
         n = r.n
+        ok_ = r.out_keys if r.out_keys is not None else sk[:n]
         d_k[:n].copy_(r.keys, non_blocking=True)
         if r.pairs:
             d_v[:n].copy_(r.vals, non_blocking=True)
             rs_sort_u32_pairs(d_k, d_v, o_k, o_v, n, num_parts, None, temp, stream)
-            r.out_vals.copy_(o_v[:n], non_blocking=True)
+            (r.out_vals if r.out_vals is not None else sv[:n]).copy_(o_v[:n], non_blocking=True)
         else:
             rs_sort_u32(d_k, o_k, n, num_parts, None, temp, stream)
-        r.out_keys.copy_(o_k[:n], non_blocking=True)
+        ok_.copy_(o_k[:n], non_blocking=True)
         stream.synchronize()
     return time.perf_counter() - t0
 
