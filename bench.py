@@ -652,8 +652,20 @@ def measure_batched(steps: int, warmup: int) -> dict:
                        device="cuda")
     stream = torch.cuda.current_stream()
 
-    def batched():
-        rs.rs_sort_u32_segmented(dk, dv, ko, vo, d_off, offs, S, n, 64, d_po, None, temp, stream)
+    # The autotuner times the segmented plans on this batch and installs the
+    # winner for its size class; the timed call passes no plan, so it runs
+    # the tuned one.  The compiled default is timed beside it.
+    from paper_cs_0004013_gb300 import tune
+    import tempfile
+    tuner = tune.Tuner(cache_path=os.path.join(tempfile.mkdtemp(), "plans.json"), reps=2)
+    tuned = tuner.best_segmented_plan(offs, pairs=True, keys=dk, vals=dv)
+    tuner.install()
+    default_plan = {"digit_bits": 8, "mode": 0, "tile": 2}
+    temp = torch.empty(max(temp.numel(), rs.rs_sort_u32_segmented(None, dv, None, vo, None, offs, S, n, 64)),
+                       dtype=torch.uint8, device="cuda")
+
+    def batched(plan=None):
+        rs.rs_sort_u32_segmented(dk, dv, ko, vo, d_off, offs, S, n, 64, d_po, plan, temp, stream)
 
     for _ in range(max(warmup, 3)):
         batched()
@@ -676,6 +688,13 @@ def measure_batched(steps: int, warmup: int) -> dict:
     rs.rs_trace_enable(False)
     trace = rs.rs_trace_read()
     t_batched = e0.elapsed_time(e1) / steps
+    batched(default_plan)
+    e0.record(stream)
+    for _ in range(steps):
+        batched(default_plan)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_default = e0.elapsed_time(e1) / steps
     # the same work captured once into a CUDA graph and replayed
     g = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
@@ -713,9 +732,14 @@ def measure_batched(steps: int, warmup: int) -> dict:
     torch.cuda.synchronize()
     t_plain = e0.elapsed_time(e1) / reps
     rs.rs_check_device_error()
+    cls = tune.size_log2(-(-n // S))
+    rs.rs_set_default_plan(rs.RS_ENTRY_SEGMENTED_PAIRS, cls, None)
     del dk, dv, ko, vo, temp, ptemp
     torch.cuda.empty_cache()
     return {"value": n / (t_batched * 1e-3) / 1e9, "unit": "Gkeys/s", "ms_per_step": t_batched,
+            "tuned_plan": tuned, "size_class": cls,
+            "default_plan": {"plan": default_plan, "value": n / (t_default * 1e-3) / 1e9, "unit": "Gkeys/s",
+                             "ms_per_step": t_default},
             "steps": steps, "workload": f"batched segmented sort: {S} key+payload arrays, log-uniform sizes in "
                                         f"[2^10, 2^20], {n} keys in total, one rs_sort_u32_segmented call",
             "segments": int(S), "n": int(n),
@@ -734,7 +758,8 @@ def run_batched(args):
             "warmup": max(args.warmup, 3), "ms_per_step": b["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": b["workload"], "segments": b["segments"], "n": b["n"]},
-            **{k: b[k] for k in ("graph_replay", "per_array_plain", "speedup_vs_per_array", "kernel_ms")}}
+            **{k: b[k] for k in ("tuned_plan", "default_plan", "graph_replay", "per_array_plain",
+                                 "speedup_vs_per_array", "kernel_ms")}}
     print(json.dumps(line), flush=True)
     return 0
 

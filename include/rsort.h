@@ -117,7 +117,14 @@ rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in,
  * num_segs * (num_parts + 1) uint64, may be NULL) receives each segment's
  * partition offsets made absolute by adding the segment start.
  * h_seg_offsets is a HOST copy of the same offsets, used to plan the
- * launches (segment classes by size) without reading device memory.        */
+ * launches (segment classes by size) without reading device memory.
+ * plan: digit_bits 0 or 8; tile 1 (512 x 16 tiled passes) or 2 (512 x 24
+ * for keys, 512 x 22 with payloads); mode MSD or automatic (every segment
+ * of up to 16,384 keys is sorted by one block in shared memory, larger ones
+ * by tiled passes) or LSD (only segments of up to 4,096 keys go to the
+ * one-block sort); key_kind as for rs_sort_u32.  Zero fields take the plan
+ * installed for the batch's size class (rs_set_default_plan), else the
+ * compiled defaults (tile 2, automatic).                                    */
 rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in,
                                 uint32_t* keys_out, uint32_t* vals_out,
                                 const uint64_t* d_seg_offsets,
@@ -279,6 +286,66 @@ rs_status rs_sort_u32_host(const uint32_t* h_keys_in, const uint32_t* h_vals_in,
 rs_status rs_sort_u32_noalloc(const uint32_t* keys_in, uint32_t* keys_out, uint64_t n,
                               uint32_t num_parts, uint64_t* h_part_offsets,
                               rs_stream_t stream);
+
+/* ---- data-adaptive plan choice (Sec. 4.2.1) ------------------------------- */
+
+/* The selection step of Sec. 4.2.1 on DEVICE keys (n of them, key words of
+ * key_kind): an evenly spaced sample of s = min(sample, n) keys (positions
+ * floor(i * n / s); the paper used 1000 points, footnote 8), each bucketed
+ * by the top `bits` bits of the sample's significant width (in the order of
+ * key_kind); the sorted sample buckets stand for the bucketed output and are
+ * split into `cells` equal ranges of sample ranks (cell c: [c*s/cells,
+ * (c+1)*s/cells)).  A cell whose sampled elements are not above its left
+ * neighbour's maximum bucket for 65 % or more of them (100 * overlap >=
+ * 65 * size) is a problem cell.  h_out (HOST, 4 words): problem cells,
+ * 1 if they are more than max_problem (clustered data), the bucket shift,
+ * s.  d_buckets (DEVICE, s words, may be NULL) receives the sorted sample
+ * buckets.  Limits: 1 <= sample <= 1024, 1 <= cells <= 1024, 1 <= bits <=
+ * 32.  Synchronises `stream`.  One selection runs at a time per process.  */
+rs_status rs_sample_overlap(const uint32_t* keys, uint64_t n, uint32_t key_kind, uint32_t bits,
+                            uint32_t sample, uint32_t cells, uint32_t max_problem,
+                            uint32_t* d_buckets, uint32_t* h_out, rs_stream_t stream);
+
+/* The plan rs_sort_u32 would run for these keys, chosen from the data: the
+ * caller's plan `base` resolved like rs_sort_u32's (installed or compiled
+ * defaults for zero fields), then the selection of Sec. 4.2.1 with the
+ * paper's parameters (1000-point sample, 64 cells, 65 %, more than two
+ * problem cells; buckets of the top 13 significant bits).  Clustered data
+ * turns a bucketing (MSD) plan into LSD, as the paper abandoned its
+ * bucketing algorithm for the clustered data set; other plans are kept.
+ * *out receives the plan, h_stats (HOST, 4 words, may be NULL) the
+ * selection's words as for rs_sample_overlap.  Synchronises `stream`.     */
+rs_status rs_choose_plan(const uint32_t* keys, uint64_t n, const rs_plan* base, rs_plan* out,
+                         uint32_t* h_stats, rs_stream_t stream);
+
+/* ---- default plans (autotuning) ------------------------------------------ */
+
+/* Entry points whose plan can be installed per size class. */
+enum {
+  RS_ENTRY_SORT_U32 = 0,         /* rs_sort_u32 and rs_sort_u32_host without payloads */
+  RS_ENTRY_SORT_U32_PAIRS = 1,   /* rs_sort_u32_pairs and rs_sort_u32_host with payloads */
+  RS_ENTRY_SEGMENTED = 2,        /* rs_sort_u32_segmented, keys only */
+  RS_ENTRY_SEGMENTED_PAIRS = 3   /* rs_sort_u32_segmented with payloads */
+};
+
+/* Installs the plan that `entry` uses for size class `size_class` (0..32)
+ * when the caller passes plan = NULL or leaves a field zero: the class of a
+ * plain sort of n keys is ceil(log2(n)), that of a segmented sort
+ * ceil(log2(mean segment size)).  plan = NULL removes the entry (the
+ * compiled defaults apply again).  key_kind must be RS_KEY_U32 (the kind
+ * always comes from the caller).  This is how the project's autotuner
+ * (paper_cs_0004013_gb300/tune.py, which times the candidates on the GPU in
+ * use) hands its choices of digit width, tile shape and MSD or LSD to the
+ * library; the paper chose its algorithm per data set by measurement too
+ * (Sec. 4.2).  Host-only; thread-safe.  For rs_sort_u32_segmented, tile is
+ * 1 (512 x 16 tiled passes) or 2 (512 x 24 for keys, 512 x 22 with
+ * payloads, the default) and mode LSD sends only segments of up to 4,096
+ * keys to the one-block sort, MSD or automatic every segment up to 16,384. */
+rs_status rs_set_default_plan(uint32_t entry, uint32_t size_class, const rs_plan* plan);
+
+/* The installed plan of (entry, size_class): *is_set = 1 and *out = the plan,
+ * or *is_set = 0 and *out zeroed.                                          */
+rs_status rs_get_default_plan(uint32_t entry, uint32_t size_class, rs_plan* out, int* is_set);
 
 /* ---- errors ------------------------------------------------------------- */
 

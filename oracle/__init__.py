@@ -34,6 +34,11 @@ its definition, so that every kernel step can be checked on its own:
 * ``skippable_digits``: a digit on which every key agrees moves nothing; the
   paper's 30-bit observation (Sec. 4.5) is the case of the top digit.
 
+* ``choose_plan``: the selection of Sec. 4.2.1 (a sample of evenly spaced
+  elements, each cell's overlap with its left neighbour's maximum, the 65 %
+  rule, more than two problem cells abandoning the bucketing algorithm),
+  written for the output partitions after bucketing by the top bits.
+
 Pins against things other than itself live in ``tests/test_oracle.py``.
 """
 from __future__ import annotations
@@ -56,6 +61,9 @@ __all__ = [
     "distribute",
     "lsd_sort",
     "msd_buckets",
+    "ordered_words",
+    "selection_sample",
+    "choose_plan",
 ]
 
 
@@ -244,3 +252,62 @@ def msd_buckets(keys, vals, shift: int, width: int):
     offs = np.zeros(h.size + 1, dtype=np.uint64)
     offs[1:] = np.cumsum(h, dtype=np.uint64)
     return k, v, offs
+
+
+def ordered_words(keys, kind: str = "u32") -> np.ndarray:
+    """32-bit words whose unsigned order is the order of ``kind``: unsigned
+    words as they are; two's-complement words with the sign bit flipped
+    (negative values below non-negative ones); binary32 words in totalOrder
+    (IEEE 754-2008 Sec. 5.10): every bit of a word with the sign bit set
+    flipped (larger magnitudes first), only the sign bit of the others."""
+    w = _u32(keys)
+    if kind == "u32":
+        return w.copy()
+    if kind == "i32":
+        return w ^ np.uint32(0x80000000)
+    if kind == "f32":
+        neg = (w >> np.uint32(31)).astype(bool)
+        return np.where(neg, ~w, w | np.uint32(0x80000000)).astype(np.uint32)
+    raise ValueError(f"ordered_words covers the 32-bit kinds, not {kind!r}")
+
+
+def selection_sample(n: int, sample: int = 1000) -> np.ndarray:
+    """Positions of the evenly spaced sample (Sec. 4.2.1; footnote 8: 1000
+    points): floor(i * n / s) for i < s = min(sample, n)."""
+    s = min(sample, n)
+    return (np.arange(s, dtype=np.uint64) * np.uint64(n)) // np.uint64(max(s, 1))
+
+
+def choose_plan(keys, kind: str = "u32", bits: int = 13, sample: int = 1000, cells: int = 64,
+                max_problem: int = 2):
+    """The selection of Sec. 4.2.1 before a bucketing (MSD) plan.
+
+    Take the evenly spaced sample; bucket each sampled key (in the order of
+    ``kind``) by the top ``bits`` of the sample's significant bits; the
+    sorted buckets stand for the bucketed output, split into ``cells``
+    equal ranges of sample ranks (the output partitions).  Each cell counts
+    its sampled elements whose bucket is not above the maximum of its left
+    neighbour: those are not separated by the bucketing.  A cell with 65 %
+    or more such elements is a problem cell; more than ``max_problem`` of
+    them mean the data is clustered and the bucketing plan is abandoned.
+
+    Returns (sorted sample buckets, problem cells, clustered)."""
+    w = ordered_words(keys, kind)
+    n = w.size
+    if n == 0:
+        return np.zeros(0, dtype=np.uint32), 0, False
+    s = w[selection_sample(n, sample)]
+    width = int(s.max()).bit_length()
+    shift = max(0, width - bits)
+    b = np.sort(s >> np.uint32(shift))
+    S = b.size
+    problem = 0
+    for p in range(1, cells):
+        lo, hi = p * S // cells, (p + 1) * S // cells
+        if hi <= lo or lo == 0:  # an empty cell, or one with no sampled element to its left
+            continue
+        left_max = b[lo - 1]
+        over = int(np.count_nonzero(b[lo:hi] <= left_max))
+        if 100 * over >= 65 * (hi - lo):
+            problem += 1
+    return b, problem, problem > max_problem

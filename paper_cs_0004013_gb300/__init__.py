@@ -27,6 +27,8 @@ __all__ = [
     "rs_sort_u32_host", "rs_sort_u64", "sort64", "rs_sort_u64_pairs", "rs_sort_u64_pairs64", "sort64_pairs", "rs_sort_u32_pairs64", "sort_pairs64", "rs_merge_u32", "merge",
     "sort", "sort_pairs", "sort_segmented", "temp_bytes",
     "STATUS_NAMES", "RS_MODE_AUTO", "RS_MODE_LSD", "RS_MODE_MSD", "RS_KEY_U32", "RS_KEY_I32", "RS_KEY_F32",
+    "rs_set_default_plan", "rs_get_default_plan", "RS_ENTRY_SORT_U32", "RS_ENTRY_SORT_U32_PAIRS",
+    "RS_ENTRY_SEGMENTED", "RS_ENTRY_SEGMENTED_PAIRS", "rs_sample_overlap", "rs_choose_plan",
 ]
 
 STATUS_NAMES = {0: "RS_OK", 1: "RS_ERR_INVALID", 2: "RS_ERR_TEMP_TOO_SMALL", 3: "RS_ERR_CUDA",
@@ -79,6 +81,10 @@ _SIGS = {
     "rs_sort_u32_noalloc": [_P, _P, _U64, _U32, _U64P, _P],
     "rs_selftest_wait_timeout": [_P, ctypes.c_size_t, _P],
     "rs_trace_read": [ctypes.POINTER(RsTraceEntry), _U32, ctypes.POINTER(ctypes.c_uint32)],
+    "rs_set_default_plan": [_U32, _U32, _PLANP],
+    "rs_sample_overlap": [_P, _U64, _U32, _U32, _U32, _U32, _U32, _P, ctypes.POINTER(ctypes.c_uint32), _P],
+    "rs_choose_plan": [_P, _U64, _PLANP, _PLANP, ctypes.POINTER(ctypes.c_uint32), _P],
+    "rs_get_default_plan": [_U32, _U32, _PLANP, ctypes.POINTER(ctypes.c_int)],
 }
 
 
@@ -329,6 +335,45 @@ def rs_sort_u32_noalloc(keys_in, keys_out, n: int, num_parts: int = 64, stream=N
     op = offs.ctypes.data_as(_U64P) if offs is not None else None
     _check(lib.rs_sort_u32_noalloc(_ptr(keys_in), _ptr(keys_out), n, num_parts, op, _stream(stream)))
     return offs
+
+
+RS_ENTRY_SORT_U32, RS_ENTRY_SORT_U32_PAIRS, RS_ENTRY_SEGMENTED, RS_ENTRY_SEGMENTED_PAIRS = 0, 1, 2, 3
+
+
+def rs_sample_overlap(keys, n: int, key_kind: int = 0, bits: int = 13, sample: int = 1000, cells: int = 64,
+                      max_problem: int = 2, d_buckets=None, stream=None) -> dict:
+    """The selection step of Sec. 4.2.1 on device keys (see include/rsort.h):
+    {"problem_cells", "clustered", "shift", "sample"}."""
+    out = (ctypes.c_uint32 * 4)()
+    _check(lib.rs_sample_overlap(_ptr(keys), n, key_kind, bits, sample, cells, max_problem, _ptr(d_buckets), out,
+                                 _stream(stream)))
+    return {"problem_cells": int(out[0]), "clustered": bool(out[1]), "shift": int(out[2]), "sample": int(out[3])}
+
+
+def rs_choose_plan(keys, n: int, plan=None, stream=None) -> tuple[dict, dict]:
+    """The plan rs_sort_u32 would run for these keys, chosen by the sample
+    of Sec. 4.2.1, and the selection's statistics."""
+    out = RsPlan()
+    st = (ctypes.c_uint32 * 4)()
+    _check(lib.rs_choose_plan(_ptr(keys), n, _plan(plan), ctypes.byref(out), st, _stream(stream)))
+    return ({"digit_bits": out.digit_bits, "mode": out.mode, "tile": out.tile, "key_kind": out.key_kind},
+            {"problem_cells": int(st[0]), "clustered": bool(st[1]), "shift": int(st[2]), "sample": int(st[3])})
+
+
+def rs_set_default_plan(entry: int, size_class: int, plan) -> None:
+    """Installs (plan dict or RsPlan) or removes (None) the plan an entry
+    point uses for a size class when called without one."""
+    _check(lib.rs_set_default_plan(entry, size_class, _plan(plan)))
+
+
+def rs_get_default_plan(entry: int, size_class: int):
+    """The installed plan of (entry, size_class) as a dict, or None."""
+    out = RsPlan()
+    is_set = ctypes.c_int(0)
+    _check(lib.rs_get_default_plan(entry, size_class, ctypes.byref(out), ctypes.byref(is_set)))
+    if not is_set.value:
+        return None
+    return {"digit_bits": out.digit_bits, "mode": out.mode, "tile": out.tile}
 
 
 def rs_check_device_error(stream=None) -> None:

@@ -43,6 +43,9 @@ rs_status cuda_fail(cudaError_t e, const char* what) {
 
 // Device error word: set by kernels whose bounded waits gave up.
 __device__ uint32_t g_err_word;
+// Where the selection kernel leaves its four result words (read back by the host).
+__device__ uint32_t g_select_out[4];
+std::mutex g_select_mu;  // one selection at a time per process (they share the result words)
 // Where take_error_kernel leaves the word it took (read back by the host).
 __device__ uint32_t g_err_taken;
 
@@ -85,11 +88,14 @@ rs_status device_state(DeviceState** out) {
     }
     RS_CUDA(prepare_hist64(), "cudaFuncSetAttribute(hist64)");
     const SegKernels* sk = seg_kernels();
-    const void* fn[8] = {sk->pass_keys,  sk->pass_pairs,  sk->tiny_keys, sk->tiny_pairs,
-                         sk->small_keys, sk->small_pairs, sk->hist,      sk->hist_xf};
-    const size_t sm[8] = {sk->pass_smem_keys,  sk->pass_smem_pairs,  sk->tiny_smem_keys, sk->tiny_smem_pairs,
-                          sk->small_smem_keys, sk->small_smem_pairs, sk->hist_smem,      sk->hist_smem};
-    for (int i = 0; i < 8; ++i)
+    const void* fn[10] = {sk->pass_keys[0], sk->pass_pairs[0], sk->pass_keys[1], sk->pass_pairs[1],
+                          sk->tiny_keys,    sk->tiny_pairs,    sk->small_keys,   sk->small_pairs,
+                          sk->hist,         sk->hist_xf};
+    const size_t sm[10] = {sk->pass_smem_keys[0], sk->pass_smem_pairs[0], sk->pass_smem_keys[1],
+                           sk->pass_smem_pairs[1], sk->tiny_smem_keys,     sk->tiny_smem_pairs,
+                           sk->small_smem_keys,    sk->small_smem_pairs,   sk->hist_smem,
+                           sk->hist_smem};
+    for (int i = 0; i < 10; ++i)
       RS_CUDA(cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm[i])),
               "cudaFuncSetAttribute(segmented)");
     st.ready = true;
@@ -101,12 +107,18 @@ rs_status device_state(DeviceState** out) {
 // ---- tracing -------------------------------------------------------------------
 enum TraceKind {
   T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_SEGPLAN, T_SEGHIST, T_SEGSCAN, T_SEGPASS, T_LOCAL,
-  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_MERGE, T_KINDS
+  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_MERGE, T_SELECT, T_KINDS
 };
 const char* const kTraceNames[T_KINDS] = {"clear",       "upfront_hist", "digit_scan", "onesweep_r8",
                                           "onesweep_r11", "seg_part_offsets", "seg_plan", "seg_hist",
                                           "seg_scan",    "seg_pass",     "local_sort", "copy_h2d",
-                                          "copy_d2h",    "split64",      "join64",     "merge"};
+                                          "copy_d2h",    "split64",      "join64",     "merge",
+                                          "select"};
+
+// The selection of Sec. 4.2.1 with the paper's parameters: a 1000-point
+// sample (footnote 8), 64 cells, 65 % overlap, more than two problem cells;
+// buckets of the top 13 significant bits (the paper's 8192 buckets, Sec. 4.7).
+constexpr uint32_t kSelectSample = 1000, kSelectCells = 64, kSelectMaxProblem = 2, kSelectBits = 13;
 struct TraceRec {
   int kind;
   double keys;
@@ -153,6 +165,43 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
   if (!a || !b || na == 0 || nb == 0) return false;
   const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
   return x < y + nb && y < x + na;
+}
+
+// ---- default plans per entry point and size class ----------------------------
+// A tuner (or the caller) may install the plan an entry point uses for a size
+// class when the caller passes no plan or leaves fields zero.  Size class =
+// ceil(log2(n)) for plain sorts, ceil(log2(mean segment size)) for segmented
+// ones.  Unset classes keep the compiled defaults.
+constexpr int kPlanEntries = 4;
+constexpr int kSizeClasses = 33;
+std::mutex g_plan_mu;
+rs_plan g_plan_table[kPlanEntries][kSizeClasses] = {};
+bool g_plan_set[kPlanEntries][kSizeClasses] = {};
+
+uint32_t size_log2(uint64_t n) {
+  uint32_t b = 0;
+  while (b < 32 && (uint64_t(1) << b) < n) ++b;
+  return b;
+}
+
+// The plan an entry point runs: the caller's nonzero fields, else the
+// installed plan's, else zero (the compiled defaults).  key_kind is always
+// the caller's (zero, unsigned, without a plan).
+rs_plan resolve_plan(int entry, uint64_t size, const rs_plan* user) {
+  rs_plan r = {0, 0, 0, 0};
+  {
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    const uint32_t c = size_log2(size);
+    if (g_plan_set[entry][c]) r = g_plan_table[entry][c];
+  }
+  r.key_kind = 0;
+  if (user) {
+    if (user->digit_bits) r.digit_bits = user->digit_bits;
+    if (user->mode) r.mode = user->mode;
+    if (user->tile) r.tile = user->tile;
+    r.key_kind = user->key_kind;
+  }
+  return r;
 }
 
 // ---- plan -------------------------------------------------------------------
@@ -390,12 +439,18 @@ struct SegLayout {
   size_t status = 0, jobs = 0, alt_k = 0, alt_v = 0, end = 0;
   size_t memset_from = 0, memset_bytes = 0;  // counts + seg_hist
   size_t tiles_ub = 0;
+  int shape = 1;  // tiled-pass shape
 };
 
-SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int nd, bool pairs) {
+// Shape of the segmented pipeline's tiled passes when a plan names none.
+constexpr int kSegDefaultShape = 1;
+
+SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int nd, bool pairs,
+                          int shape = kSegDefaultShape) {
   const SegKernels* sk = seg_kernels();
   SegLayout L;
-  L.tiles_ub = size_t((total_n + sk->tile(pairs) - 1) / sk->tile(pairs)) + num_segs;
+  L.shape = shape;
+  L.tiles_ub = size_t((total_n + sk->tile(pairs, shape) - 1) / sk->tile(pairs, shape)) + num_segs;
   off = align_up(off);
   L.counts = off;
   L.memset_from = off;
@@ -427,10 +482,15 @@ SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int n
   return L;
 }
 
+// small_max: segments up to this many keys are sorted by one block in shared
+// memory (at most the local sort's capacity); larger ones by tiled passes.
 rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t* kin, const uint32_t* vin,
                         uint32_t* kout, uint32_t* vout, const uint64_t* seg_off, uint32_t num_segs, int nd,
-                        KeyXform xin, KeyXform xout, DeviceState* ds, cudaStream_t s) {
+                        KeyXform xin, KeyXform xout, DeviceState* ds, cudaStream_t s, uint32_t small_max = 0) {
   const SegKernels* sk = seg_kernels();
+  if (small_max == 0 || small_max > sk->small_max) small_max = sk->small_max;
+  const uint32_t tiny_max = small_max < sk->tiny_max ? small_max : sk->tiny_max;
+  const uint32_t seg_tile = sk->tile(vin != nullptr, L.shape);
   const bool pairs = vin != nullptr;
   uint32_t* counts = reinterpret_cast<uint32_t*>(temp + L.counts);
   const unsigned sms = unsigned(ds->num_sms);
@@ -439,9 +499,9 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
           "cudaMemsetAsync(segment counts)");
   SegPlanArgs pa{seg_off,
                  num_segs,
-                 sk->tiny_max,
-                 sk->small_max,
-                 sk->tile(pairs),
+                 tiny_max,
+                 small_max,
+                 seg_tile,
                  reinterpret_cast<uint32_t*>(temp + L.large_seg),
                  reinterpret_cast<uint32_t*>(temp + L.tile_prefix),
                  reinterpret_cast<uint32_t*>(temp + L.small_seg),
@@ -456,7 +516,7 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
   ha.large_seg = pa.large_seg;
   ha.tile_prefix = pa.tile_prefix;
   ha.counts = counts;
-  ha.tile = sk->tile(pairs);
+  ha.tile = seg_tile;
   ha.num_digits = nd;
   for (int j = 0; j < nd; ++j) ha.dig[j] = dig[j];
   ha.seg_hist = reinterpret_cast<uint32_t*>(temp + L.seg_hist);
@@ -493,7 +553,7 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
     ga.xin = p == 0 ? xin : kIdentityXform;
     ga.xout = p == nd - 1 ? xout : kIdentityXform;
     RS_CUDA(traced(T_SEGPASS, 0, s,
-                   [&] { return launch_seg_pass(ga, pairs, cap(L.tiles_ub, size_t(sms) * 2), s); }),
+                   [&] { return launch_seg_pass(ga, pairs, L.shape, cap(L.tiles_ub, size_t(sms) * 2), s); }),
             "launch seg_pass");
     src_k = ga.kout;
     src_v = ga.vout;
@@ -627,9 +687,11 @@ rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in
 }
 
 rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
-                    uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets, const rs_plan* plan, void* temp,
+                    uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets, const rs_plan* user_plan, void* temp,
                     size_t* temp_bytes, cudaStream_t s, bool pairs) {
   g_last_error.clear();
+  const rs_plan eff = resolve_plan(pairs ? RS_ENTRY_SORT_U32_PAIRS : RS_ENTRY_SORT_U32, n, user_plan);
+  const rs_plan* plan = &eff;
   rs_status st = check_common(keys_in, keys_out, n, temp, temp_bytes);
   if (st != RS_OK) return st;
   if (num_parts < 1) return fail(RS_ERR_INVALID, "num_parts must be >= 1");
@@ -678,7 +740,7 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   // sorted in shared memory by one launch (no histogram, scans or tiled
   // passes), which is several times faster for such sizes.
   const SegKernels* sk = seg_kernels();
-  const bool automatic = !plan || (plan->digit_bits == 0 && plan->mode == RS_MODE_AUTO && plan->tile == 0);
+  const bool automatic = plan->digit_bits == 0 && plan->mode == RS_MODE_AUTO && plan->tile == 0;
   if (automatic && n <= sk->small_max) {
     LocalArgs la{};
     la.kin = keys_in;
@@ -1186,13 +1248,22 @@ rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in
       if (m > max_seg) max_seg = m;
     }
   }
-  if (plan && plan->digit_bits && plan->digit_bits != 8)
-    return fail(RS_ERR_UNSUPPORTED, "the segmented sort uses 8-bit digits");
+  const rs_plan eff = resolve_plan(pairs ? RS_ENTRY_SEGMENTED_PAIRS : RS_ENTRY_SEGMENTED,
+                                   num_segs ? (total_n + num_segs - 1) / num_segs : 0, plan);
+  if (eff.digit_bits && eff.digit_bits != 8) return fail(RS_ERR_UNSUPPORTED, "the segmented sort uses 8-bit digits");
+  if (eff.tile > uint32_t(kSegShapes))
+    return fail(RS_ERR_UNSUPPORTED, "the segmented sort has tile shapes 1 to %d (got %u)", kSegShapes, eff.tile);
+  if (eff.mode > RS_MODE_MSD) return fail(RS_ERR_INVALID, "unknown mode %u", eff.mode);
+  const int shape = eff.tile ? int(eff.tile) - 1 : kSegDefaultShape;
+  // MSD (and automatic): every segment that fits one block is sorted there
+  // (bucket, then local sort); LSD: only the smallest class is, larger
+  // segments go through the tiled passes.
+  const uint32_t small_max = eff.mode == RS_MODE_LSD ? seg_kernels()->tiny_max : seg_kernels()->small_max;
   KeyXform xf;
-  if (rs_status st = key_xform(plan, &xf); st != RS_OK) return st;
+  if (rs_status st = key_xform(&eff, &xf); st != RS_OK) return st;
   if (needs_wide_status(total_n)) return fail(RS_ERR_UNSUPPORTED, "the segmented sort needs total_n < 2^30 - 2^16");
   (void)max_seg;
-  const SegLayout L = make_seg_layout(0, num_segs, total_n, 4, pairs);
+  const SegLayout L = make_seg_layout(0, num_segs, total_n, 4, pairs, shape);
   if (!temp) {
     *temp_bytes = L.end;
     return RS_OK;
@@ -1223,7 +1294,7 @@ rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in
   }
   if (total_n == 0) return RS_OK;
   return run_segmented(L, static_cast<unsigned char*>(temp), keys_in, pairs ? vals_in : nullptr, keys_out,
-                       pairs ? vals_out : nullptr, d_seg_offsets, num_segs, 4, xf, xf, ds, s);
+                       pairs ? vals_out : nullptr, d_seg_offsets, num_segs, 4, xf, xf, ds, s, small_max);
 }
 
 rs_status rs_digit_histograms(const uint32_t* keys, uint64_t n, uint32_t digit_bits, uint32_t* d_hist,
@@ -1303,6 +1374,80 @@ rs_status rs_radix_pass(const uint32_t* keys_in, const uint32_t* vals_in, uint32
   if (st != RS_OK) return st;
   return run_lsd(p, L, keys_in, vals_in, keys_out, vals_out, uint32_t(n), static_cast<unsigned char*>(temp), true,
                  ds, s);
+}
+
+rs_status rs_sample_overlap(const uint32_t* keys, uint64_t n, uint32_t key_kind, uint32_t bits, uint32_t sample,
+                            uint32_t cells, uint32_t max_problem, uint32_t* d_buckets, uint32_t* h_out,
+                            rs_stream_t stream) {
+  g_last_error.clear();
+  if (!h_out) return fail(RS_ERR_INVALID, "h_out is NULL");
+  if (n > 0 && !keys) return fail(RS_ERR_INVALID, "NULL keys");
+  if (reinterpret_cast<uintptr_t>(keys) & 3) return fail(RS_ERR_INVALID, "keys must be 4-byte aligned");
+  if (bits < 1 || bits > 32) return fail(RS_ERR_INVALID, "bits must be 1..32 (got %u)", bits);
+  if (sample < 1 || sample > 1024) return fail(RS_ERR_INVALID, "sample must be 1..1024 (got %u)", sample);
+  if (cells < 1 || cells > 1024) return fail(RS_ERR_INVALID, "cells must be 1..1024 (got %u)", cells);
+  const rs_plan kind_only = {0, 0, 0, key_kind};
+  KeyXform xf;
+  if (rs_status st = key_xform(&kind_only, &xf); st != RS_OK) return st;
+  if (n == 0) {
+    h_out[0] = h_out[1] = h_out[2] = h_out[3] = 0;
+    return RS_OK;
+  }
+  DeviceState* ds = nullptr;
+  if (rs_status st = device_state(&ds); st != RS_OK) return st;
+  const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_select_mu);
+  uint32_t* d_out = nullptr;
+  RS_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&d_out), g_select_out), "cudaGetSymbolAddress(select)");
+  SelectArgs a{keys, n, xf, bits, sample, cells, max_problem, d_out, d_buckets};
+  RS_CUDA(traced(T_SELECT, double(n), s, [&] { return launch_select(a, s); }), "launch select");
+  RS_CUDA(cudaMemcpyAsync(h_out, d_out, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "read selection");
+  RS_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+  return RS_OK;
+}
+
+rs_status rs_choose_plan(const uint32_t* keys, uint64_t n, const rs_plan* base, rs_plan* out, uint32_t* h_stats,
+                         rs_stream_t stream) {
+  g_last_error.clear();
+  if (!out) return fail(RS_ERR_INVALID, "out is NULL");
+  const rs_plan eff = resolve_plan(RS_ENTRY_SORT_U32, n, base);
+  uint32_t st4[4] = {0, 0, 0, 0};
+  if (rs_status st = rs_sample_overlap(keys, n, eff.key_kind, kSelectBits, kSelectSample, kSelectCells,
+                                       kSelectMaxProblem, nullptr, st4, stream);
+      st != RS_OK)
+    return st;
+  *out = eff;
+  if (st4[1] && eff.mode == RS_MODE_MSD) out->mode = RS_MODE_LSD;  // clustered: no bucketing plan
+  if (h_stats)
+    for (int i = 0; i < 4; ++i) h_stats[i] = st4[i];
+  return RS_OK;
+}
+
+rs_status rs_set_default_plan(uint32_t entry, uint32_t size_class, const rs_plan* plan) {
+  g_last_error.clear();
+  if (entry >= uint32_t(kPlanEntries)) return fail(RS_ERR_INVALID, "unknown entry %u", entry);
+  if (size_class >= uint32_t(kSizeClasses)) return fail(RS_ERR_INVALID, "size class %u above 32", size_class);
+  if (plan) {
+    if (plan->key_kind != RS_KEY_U32) return fail(RS_ERR_INVALID, "a default plan does not set key_kind");
+    if (plan->mode > RS_MODE_MSD) return fail(RS_ERR_INVALID, "unknown mode %u", plan->mode);
+    if (plan->digit_bits && plan->digit_bits != 8 && plan->digit_bits != 11)
+      return fail(RS_ERR_UNSUPPORTED, "digit_bits must be 0, 8 or 11 (got %u)", plan->digit_bits);
+  }
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  g_plan_set[entry][size_class] = plan != nullptr;
+  g_plan_table[entry][size_class] = plan ? *plan : rs_plan{0, 0, 0, 0};
+  return RS_OK;
+}
+
+rs_status rs_get_default_plan(uint32_t entry, uint32_t size_class, rs_plan* out, int* is_set) {
+  g_last_error.clear();
+  if (!out || !is_set) return fail(RS_ERR_INVALID, "NULL output");
+  if (entry >= uint32_t(kPlanEntries)) return fail(RS_ERR_INVALID, "unknown entry %u", entry);
+  if (size_class >= uint32_t(kSizeClasses)) return fail(RS_ERR_INVALID, "size class %u above 32", size_class);
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  *is_set = g_plan_set[entry][size_class] ? 1 : 0;
+  *out = g_plan_table[entry][size_class];
+  return RS_OK;
 }
 
 const char* rs_last_error(void) { return g_last_error.c_str(); }

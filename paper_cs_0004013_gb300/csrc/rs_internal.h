@@ -225,12 +225,16 @@ struct LocalArgs {
   KeyXform xin, xout;     // applied on loading kin, inverted on storing kout
 };
 
+// Tiled-pass shapes of the segmented pipeline (rs_plan.tile = shape + 1).
+constexpr int kSegShapes = 2;
+
 struct SegKernels {
-  uint32_t tile_keys, tile_pairs, tiny_max, small_max;
-  uint32_t tile(bool pairs) const { return pairs ? tile_pairs : tile_keys; }
-  size_t pass_smem_keys, pass_smem_pairs, tiny_smem_keys, tiny_smem_pairs, small_smem_keys, small_smem_pairs;
-  const void* pass_keys;
-  const void* pass_pairs;
+  uint32_t tile_keys[kSegShapes], tile_pairs[kSegShapes], tiny_max, small_max;
+  uint32_t tile(bool pairs, int shape) const { return pairs ? tile_pairs[shape] : tile_keys[shape]; }
+  size_t pass_smem_keys[kSegShapes], pass_smem_pairs[kSegShapes];
+  size_t tiny_smem_keys, tiny_smem_pairs, small_smem_keys, small_smem_pairs;
+  const void* pass_keys[kSegShapes];
+  const void* pass_pairs[kSegShapes];
   const void* tiny_keys;
   const void* tiny_pairs;
   const void* small_keys;
@@ -244,7 +248,7 @@ const SegKernels* seg_kernels();
 cudaError_t launch_seg_plan(const SegPlanArgs& a, cudaStream_t s);
 cudaError_t launch_seg_hist(const SegHistArgs& a, unsigned grid, cudaStream_t s);
 cudaError_t launch_seg_scan(const SegScanArgs& a, unsigned grid, cudaStream_t s);
-cudaError_t launch_seg_pass(const SegPassArgs& a, bool pairs, unsigned grid, cudaStream_t s);
+cudaError_t launch_seg_pass(const SegPassArgs& a, bool pairs, int shape, unsigned grid, cudaStream_t s);
 cudaError_t launch_local_sort(const LocalArgs& a, bool small, bool pairs, unsigned grid, cudaStream_t s);
 cudaError_t launch_bases_to_offsets(const uint32_t* bases, uint32_t num, uint64_t n, uint64_t* seg_off,
                                     cudaStream_t s);
@@ -268,6 +272,21 @@ cudaError_t launch_merge(const MergeArgs& m, cudaStream_t s);
 
 cudaError_t launch_split64(const WideArgs& a, unsigned grid, cudaStream_t s);
 cudaError_t launch_join64(const WideArgs& a, unsigned grid, cudaStream_t s);
+
+// The selection of Sec. 4.2.1 (select.cu): an evenly spaced sample of at
+// most 1024 keys, bucketed by the top `bits` of its significant width;
+// out[0] = problem cells, out[1] = 1 if more than max_problem, out[2] = the
+// bucket shift, out[3] = the sample size; buckets (may be null) receives the
+// sorted sample buckets.
+struct SelectArgs {
+  const uint32_t* keys;
+  uint64_t n;
+  KeyXform x;
+  uint32_t bits, sample, cells, max_problem;
+  uint32_t* out;      // [4], device
+  uint32_t* buckets;  // [sample] or null, device
+};
+cudaError_t launch_select(const SelectArgs& a, cudaStream_t s);
 
 // Self-test of the bounded lookback wait (selftest.cu).
 cudaError_t launch_lookback_timeout(const uint32_t* status, uint32_t* err, cudaStream_t s);

@@ -159,13 +159,19 @@ class SortServer:
     robin; mem_budget: bytes of device memory the server may hold for
     in-flight batches (inputs, outputs and temp); max_batch_keys: largest
     batch arena in keys; direct_min_keys: requests this large are sorted on
-    their own, from and into their pinned buffers."""
+    their own, from and into their pinned buffers; tuner: a tune.Tuner whose
+    cached plans are installed in the library for the server's calls."""
 
     def __init__(self, slots: int = 8, streams: int = 8, mem_budget: int = 8 << 30,
                  max_batch_keys: int = 1 << 24, num_parts: int = 64, device: str = "cuda",
-                 direct_min_keys: int = 1 << 22, result_pool: ResultPool | None = None, on_done=None):
+                 direct_min_keys: int = 1 << 22, result_pool: ResultPool | None = None, on_done=None,
+                 tuner=None):
         import torch
         self.result_pool, self.on_done = result_pool, on_done
+        # A tuner's cached choices (digit width, tile shape, MSD or LSD per
+        # size class) become the library's plans for calls without one: the
+        # server's segmented batches and direct sorts pass no plan.
+        self.tuned_plans = tuner.install() if tuner is not None else 0
         self.device = torch.device(device)
         self.slots, self.mem_budget, self.max_batch_keys = slots, mem_budget, max_batch_keys
         self.direct_min_keys = direct_min_keys

@@ -498,3 +498,83 @@ def test_merge_is_the_textbook_merge(kind, sizes):
                                 lambda x, y: x < y)
     ko, vo = oracle.merge(a, b, va, vb, kind)
     assert [conv(x) for x in ko] == wk and list(vo) == wv
+
+
+# ---------------------------------------------- the selection of Sec. 4.2.1
+def read_golden_selection():
+    cases, cur = [], None
+    for line in open(os.path.join(GOLDEN, "selection_example.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line == "case":
+            cur = {}
+            cases.append(cur)
+            continue
+        k, *v = line.split()
+        cur[k] = [int(x) for x in v]
+    return cases
+
+
+def test_golden_selection_examples():
+    cases = read_golden_selection()
+    assert len(cases) == 4
+    for c in cases:
+        b, problem, clustered = oracle.choose_plan(np.array(c["keys"], dtype=np.uint32), "u32", bits=c["bits"][0],
+                                                   sample=c["sample"][0], cells=c["cells"][0],
+                                                   max_problem=c["max_problem"][0])
+        assert [int(x) for x in b] == c["buckets"], c
+        assert problem == c["problem"][0] and int(clustered) == c["clustered"][0], c
+
+
+def test_selection_sample_positions_are_evenly_spaced():
+    assert list(oracle.selection_sample(12, 4)) == [0, 3, 6, 9]
+    assert list(oracle.selection_sample(5, 1000)) == [0, 1, 2, 3, 4]  # fewer keys than the sample: all of them
+    pos = oracle.selection_sample(10 ** 9, 1000)
+    assert pos.size == 1000 and pos[0] == 0 and np.all(np.diff(pos.astype(np.int64)) >= 10 ** 6 - 1)
+
+
+def test_ordered_words_give_each_kinds_order():
+    rng = np.random.default_rng(3)
+    w = rng.integers(0, 1 << 32, 5000, dtype=np.uint64).astype(np.uint32)
+    w[:8] = [0, 1, 0x7FFFFFFF, 0x80000000, 0x80000001, 0xFFFFFFFF, 0x7F800000, 0xFF800000]
+    for kind in ("u32", "i32", "f32"):
+        o = oracle.ordered_words(w, kind)
+        assert np.array_equal(np.argsort(o, kind="stable"), oracle.order_perm(w, kind)), kind
+
+
+def test_selection_threshold_is_65_percent_inclusive():
+    """A cell of 20 sampled elements with 13 in its left neighbour's last
+    bucket (65 %) is a problem cell; with 12 (60 %) it is not."""
+    for copies, want in ((14, 1), (13, 0)):
+        keys = np.concatenate([np.arange(19), np.full(copies, 19), np.arange(100, 100 + 40 - 19 - copies)])
+        keys = keys.astype(np.uint32)
+        assert keys.size == 40
+        _, problem, _ = oracle.choose_plan(keys, bits=32, sample=40, cells=2, max_problem=0)
+        assert problem == want, copies
+
+
+def test_selection_on_the_workloads():
+    """Uniform keys spread over the buckets: no problem cell.  Tight clusters
+    (eight windows of 4096 values) cannot be separated by 13-bit buckets:
+    most cells are problem cells and the bucketing plan is abandoned, as for
+    the paper's fifth data set.  Equal keys: every cell after the first."""
+    n = 1 << 18
+    _, p, c = oracle.choose_plan(synth.uniform31(n, 1))
+    assert p == 0 and not c
+    _, p, c = oracle.choose_plan(synth.tight_clusters(n, 1))
+    assert p > 2 and c
+    _, p, c = oracle.choose_plan(np.full(5000, 77, np.uint32))
+    assert p == 63 and c
+    # all sampled keys distinct and buckets as fine as the keys: no overlap
+    _, p, _ = oracle.choose_plan(np.arange(5000, dtype=np.uint32) * np.uint32(7), bits=32)
+    assert p == 0
+
+
+def test_selection_with_fewer_sampled_keys_than_cells():
+    """With fewer sampled keys than cells, most cells are empty and the first
+    non-empty one starts at rank 0: it has no left neighbour to overlap."""
+    _, p, _ = oracle.choose_plan(np.array([5], np.uint32))
+    assert p == 0
+    _, p, _ = oracle.choose_plan(np.array([5, 5], np.uint32))  # cells 31 (rank 0) and 63 (rank 1)
+    assert p == 1
