@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--n", type=int, default=N_KEYS, help="keys per sort (default 2^26)")
     ap.add_argument("--digit-bits", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--mode", choices=["auto", "lsd", "msd"], default="auto",
+                    help="msd: bucket by bits 18-31, then sort each bucket (the MSD plan)")
     ap.add_argument("--pairs", action="store_true", help="time key+payload sorts as the main value")
     ap.add_argument("--keys64", action="store_true", help="64-bit keys (rs_sort_u64), uniform over all 2^64 words")
     ap.add_argument("--vals64", action="store_true",
@@ -322,7 +324,8 @@ def run_ours(args):
         keys = workload_keys(n, synth.CONFIG_SEED + 2 + 1000 * rank, args.key_kind)
         d_keys = torch.from_numpy(keys.view(np.int32)).to(dev)
     d_out = torch.empty_like(d_keys)
-    plan = {"digit_bits": args.digit_bits, "tile": args.tile, "key_kind": KEY_KINDS[args.key_kind]}
+    plan = {"digit_bits": args.digit_bits, "tile": args.tile, "key_kind": KEY_KINDS[args.key_kind],
+            "mode": {"auto": 0, "lsd": 1, "msd": 2}[args.mode]}
     vals64 = args.vals64 and not wide
     wide_v64 = args.vals64 and wide  # 64-bit keys with 64-bit values
     pairs = args.pairs or args.vals64
@@ -454,7 +457,26 @@ def run_ours(args):
         bpk = (32 if split else 0) + 4 + passes * word_bytes
     peak, peak_kind = measured_peak()
     roof = None
-    if pass_kind:
+    msd = args.mode == "msd" and not wide and not vals64
+    if msd:
+        # MSD plan, every bucket within the local sort (uniform keys): keys
+        # only: count read 4 + distribution 8 + local sort 8 = 20 B/key;
+        # key+value: LSD histograms 4 + two stable passes 2 x 16 + count 4 +
+        # local sort 16 = 56 B/key.  The roofline kernel is the one with the
+        # most time per sort, against its own algorithmic bytes per sort.
+        bpk = 56 if pairs else 20
+        per_sort = {"msd_count": 4 * n, "msd_scatter": 8 * n, "local_sort": (16 if pairs else 8) * n,
+                    "onesweep_r8": 2 * 16 * n, "upfront_hist": 4 * n}
+        kind = max((k for k in trace if k in per_sort), key=lambda k: trace[k]["total_ms"], default=None)
+        if kind:
+            k_ms = trace[kind]["total_ms"] / args.steps
+            achieved = per_sort[kind] / (k_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": kind, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_sort": per_sort[kind], "ms_per_sort": k_ms,
+                    "launches_per_sort": trace[kind]["launches"] / args.steps}
+        passes = 0
+    if pass_kind and not msd:
         tr = trace[pass_kind]
         avg_ms = tr["total_ms"] / tr["launches"]
         bytes_launch = word_bytes * tr["keys"] / tr["launches"]
@@ -546,7 +568,7 @@ def run_ours(args):
     # (config 5), each against its per-request plain launches.
     extra = {}
     headline = (world == 1 and not wide and not vals64 and not pairs and args.key_kind == "u32" and n == N_KEYS
-                and not args.digit_bits and not args.tile)
+                and not args.digit_bits and not args.tile and args.mode == "auto")
     if rank == 0 and headline and not args.no_extra:
         extra["pairs"] = measure_pairs(d_keys, args.steps, peak)
         del d_out, temp
@@ -564,7 +586,7 @@ def run_ours(args):
                                     workload_label(n, pairs).replace("uint32 keys uniform in [0, 2^31-1]",
                                                                      "uint64 keys uniform over all 2^64 values")
                                     .replace("key+payload", "key+64-bit value" if wide_v64 else "key+payload")),
-                       "n": n, "digit_bits": args.digit_bits or "auto", "passes": passes,
+                       "n": n, "digit_bits": args.digit_bits or "auto", "mode": args.mode, "passes": passes,
                        "algorithmic_bytes_per_key": bpk,
                        "sort_roofline_frac": value / world * 1e9 * bpk / (peak * 1e9),
                        "l2": (f"inputs ({4 * n / 1e6:.0f} MB) exceed L2 ({L2_BYTES / 1e6:.0f} MB); no flush"
@@ -577,6 +599,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": launches,
             "kernel_ms": {k: v["total_ms"] / max(v["launches"], 1) for k, v in trace.items()},
+            "kernel_ms_per_step": {k: v["total_ms"] / args.steps for k, v in trace.items()},
             "clocks": clock_summary,
             **extra,
         }

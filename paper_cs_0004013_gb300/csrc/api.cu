@@ -87,6 +87,9 @@ rs_status device_state(DeviceState** out) {
                   "cudaFuncSetAttribute(hist)");
     }
     RS_CUDA(prepare_hist64(), "cudaFuncSetAttribute(hist64)");
+    for (const void* f : {msd_count_func(), msd_scatter_func()})
+      RS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(msd_smem())),
+              "cudaFuncSetAttribute(msd)");
     const SegKernels* sk = seg_kernels();
     const void* fn[10] = {sk->pass_keys[0], sk->pass_pairs[0], sk->pass_keys[1], sk->pass_pairs[1],
                           sk->tiny_keys,    sk->tiny_pairs,    sk->small_keys,   sk->small_pairs,
@@ -107,13 +110,13 @@ rs_status device_state(DeviceState** out) {
 // ---- tracing -------------------------------------------------------------------
 enum TraceKind {
   T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_SEGPLAN, T_SEGHIST, T_SEGSCAN, T_SEGPASS, T_LOCAL,
-  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_MERGE, T_SELECT, T_KINDS
+  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_MERGE, T_SELECT, T_MSDCOUNT, T_MSDSCAN, T_MSDSCATTER, T_KINDS
 };
 const char* const kTraceNames[T_KINDS] = {"clear",       "upfront_hist", "digit_scan", "onesweep_r8",
                                           "onesweep_r11", "seg_part_offsets", "seg_plan", "seg_hist",
                                           "seg_scan",    "seg_pass",     "local_sort", "copy_h2d",
                                           "copy_d2h",    "split64",      "join64",     "merge",
-                                          "select"};
+                                          "select",      "msd_count",    "msd_scan",   "msd_scatter"};
 
 // The selection of Sec. 4.2.1 with the paper's parameters: a 1000-point
 // sample (footnote 8), 64 cells, 65 % overlap, more than two problem cells;
@@ -593,97 +596,84 @@ rs_status check_common(const void* keys_in, const void* keys_out, uint64_t n, vo
 
 
 // ---- the MSD plan ---------------------------------------------------------------
-// upfront histogram + scans of all four bytes, one tiled pass on the top
-// byte (input -> bucket buffer), then the segmented pipeline on the 256
-// buckets over the three low bytes (bucket buffer -> output).
+// Bucketing by the keys' bits 18-31 (2^14 buckets), then the segmented
+// pipeline on the buckets over the three low bytes: a one-block local sort
+// for buckets of up to 16,384 keys, tiled passes for larger ones.
+//   keys only:  count per (chunk, bucket) [msd.cu] -> column and base scans
+//               -> one distribution pass [msd.cu] -> segmented pipeline;
+//   key+value:  two stable LSD passes over bits 18-24 and 25-31 (the
+//               distribution must keep equal keys in input order), the same
+//               count and scans for the bucket offsets -> segmented pipeline.
+constexpr uint32_t kMsdChunks = 304;  // blocks of the count and distribution kernels
+constexpr uint32_t kMsdBuckets = 1u << (32 - kMsdShift);
+
 struct MsdLayout {
-  Layout base;          // control, histograms, bases, status of the top-byte pass
+  Layout lsd;             // key+value: control, histograms, status and alternate buffers of the two passes
+  SortPlan q;             // key+value: the two-pass plan
   size_t bk = 0, bv = 0;  // bucket buffers (keys, values)
-  size_t seg_off = 0;   // [257] uint64 bucket offsets
+  size_t mhist = 0, mtot = 0, seg_off = 0;
   SegLayout seg;
   size_t total = 0;
 };
 
-MsdLayout make_msd_layout(const SortPlan& p, uint64_t n, bool pairs) {
+rs_status make_msd_layout(const SortPlan& p, uint64_t n, bool pairs, MsdLayout* out) {
   MsdLayout M;
-  SortPlan q = p;
-  q.nd = 1;  // no alternate buffer: the top-byte pass writes the bucket buffer
-  M.base = make_layout(q, n, pairs);
-  // make_layout sized histograms for one digit: widen to four
-  const size_t digits = 256;
   size_t off = 0;
-  M.base.ctrl = off;
-  off += kAlign;
-  M.base.hist = off;
-  off = align_up(off + size_t(p.nd) * digits * 4);
-  M.base.memset_bytes = off;
-  M.base.bases = off;
-  off = align_up(off + size_t(p.nd) * digits * 4);
-  M.base.status = off;
-  off = align_up(off + M.base.status_bytes);
+  if (pairs) {
+    M.q = p;
+    M.q.msd = false;
+    M.q.nd = 2;
+    M.q.dig[0] = DigitSpec{kMsdShift, 7u};
+    M.q.dig[1] = DigitSpec{kMsdShift + 7u, 32u - kMsdShift - 7u};
+    if (rs_status st = pick_kernel(8, 1, 1, needs_wide_status(n), &M.q.k); st != RS_OK) return st;
+    M.q.num_tiles = (n + M.q.k->tile - 1) / M.q.k->tile;
+    M.lsd = make_layout(M.q, n, true);
+    off = M.lsd.total;
+  }
   M.bk = off;
   off = align_up(off + size_t(n) * 4);
   if (pairs) {
     M.bv = off;
     off = align_up(off + size_t(n) * 4);
   }
+  M.mhist = off;
+  off = align_up(off + size_t(kMsdChunks) * kMsdBuckets * 4);
+  M.mtot = off;
+  off = align_up(off + size_t(kMsdBuckets) * 4);
   M.seg_off = off;
-  off = align_up(off + 257 * 8);
-  M.seg = make_seg_layout(off, 256, n, p.nd - 1, pairs);
+  off = align_up(off + (size_t(kMsdBuckets) + 1) * 8);
+  M.seg = make_seg_layout(off, kMsdBuckets, n, 3, pairs);
   M.total = M.seg.end;
-  return M;
+  *out = M;
+  return RS_OK;
 }
 
 rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in, const uint32_t* vals_in,
                   uint32_t* keys_out, uint32_t* vals_out, uint32_t n, unsigned char* temp, DeviceState* ds,
                   cudaStream_t s) {
   const bool pairs = vals_in != nullptr;
-  uint32_t* ctrl = reinterpret_cast<uint32_t*>(temp + M.base.ctrl);
-  uint32_t* hist = reinterpret_cast<uint32_t*>(temp + M.base.hist);
-  uint32_t* bases = reinterpret_cast<uint32_t*>(temp + M.base.bases);
   uint32_t* bk = reinterpret_cast<uint32_t*>(temp + M.bk);
   uint32_t* bv = pairs ? reinterpret_cast<uint32_t*>(temp + M.bv) : nullptr;
-  uint64_t* seg_off = reinterpret_cast<uint64_t*>(temp + M.seg_off);
-  const int top = p.nd - 1;
-  RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, M.base.memset_bytes, s); }),
-          "cudaMemsetAsync(temp)");
-  HistArgs ha{};
-  ha.keys = keys_in;
-  ha.n = n;
-  ha.num_digits = 1;
-  ha.dig[0] = p.dig[top];
-  ha.hist = hist + size_t(top) * 256;
-  ha.xform = p.xf;
-  ha.zero_ptr = reinterpret_cast<uint4*>(temp + M.base.status);
-  ha.zero_vec4 = M.base.status_bytes / 16;
-  const size_t work = (size_t(n) + 4095) / 4096;
-  unsigned hgrid = unsigned(ds->num_sms);
-  if (work < hgrid) hgrid = unsigned(work > 0 ? work : 1);
-  RS_CUDA(traced(T_HIST, n, s, [&] { return hist_kernel(8)->launch(ha, hgrid, s); }), "launch upfront_hist");
-  ScanArgs sa{hist + size_t(top) * 256, bases + size_t(top) * 256, nullptr, n};
-  RS_CUDA(traced(T_SCAN, 0, s, [&] { return scan_kernel(8)->launch(sa, 1u, s); }), "launch digit_scan");
-  PassArgs pa{};
-  pa.keys_in = keys_in;
-  pa.keys_out = bk;
-  pa.keys_alt = bk;
-  pa.vals_in = vals_in;
-  pa.vals_out = bv;
-  pa.vals_alt = bv;
-  pa.n = n;
-  pa.shift = p.dig[top].shift;
-  pa.width = p.dig[top].width;
-  pa.pass = 0;
-  pa.num_passes = 1;
-  pa.bases = bases + size_t(top) * 256;
-  pa.skip = nullptr;
-  pa.status = temp + M.base.status;
-  pa.tile_counter = ctrl;
-  pa.err = ds->err;
-  pa.xin = p.xf;              // the bucket buffer keeps the mapped keys,
-  pa.xout = kIdentityXform;   // the local stage maps them back
-  RS_CUDA(traced(T_PASS8, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }), "launch onesweep (top)");
-  RS_CUDA(launch_bases_to_offsets(bases + size_t(top) * 256, 256, n, seg_off, s), "launch bucket offsets");
-  return run_segmented(M.seg, temp, bk, bv, keys_out, vals_out, seg_off, 256, p.nd - 1, kIdentityXform, p.xf, ds, s);
+  MsdArgs ma{};
+  ma.keys = keys_in;
+  ma.n = n;
+  ma.x = p.xf;
+  ma.chunks = kMsdChunks;
+  ma.hist = reinterpret_cast<uint32_t*>(temp + M.mhist);
+  ma.totals = reinterpret_cast<uint32_t*>(temp + M.mtot);
+  ma.seg_off = reinterpret_cast<uint64_t*>(temp + M.seg_off);
+  ma.out = bk;
+  ma.err = ds->err;
+  RS_CUDA(traced(T_MSDCOUNT, n, s, [&] { return launch_msd_count(ma, s); }), "launch msd_count");
+  RS_CUDA(traced(T_MSDSCAN, 0, s, [&] { return launch_msd_scan(ma, s); }), "launch msd_scan");
+  if (!pairs) {
+    RS_CUDA(traced(T_MSDSCATTER, n, s, [&] { return launch_msd_scatter(ma, s); }), "launch msd_scatter");
+    // the bucket buffer holds order-mapped keys; the local phase maps them back
+    return run_segmented(M.seg, temp, bk, nullptr, keys_out, nullptr, ma.seg_off, kMsdBuckets, 3, kIdentityXform,
+                         p.xf, ds, s);
+  }
+  if (rs_status st = run_lsd(M.q, M.lsd, keys_in, vals_in, bk, bv, n, temp, true, ds, s); st != RS_OK) return st;
+  return run_segmented(M.seg, temp, bk, bv, keys_out, vals_out, ma.seg_off, kMsdBuckets, 3, p.xf, p.xf, ds, s);
 }
 
 rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
@@ -701,7 +691,7 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   Layout L = make_layout(p, n, pairs);
   MsdLayout M;
   if (p.msd) {
-    M = make_msd_layout(p, n, pairs);
+    if (rs_status st2 = make_msd_layout(p, n, pairs, &M); st2 != RS_OK) return st2;
     L.total = M.total;
   }
   if (!temp) {

@@ -273,6 +273,27 @@ cudaError_t launch_merge(const MergeArgs& m, cudaStream_t s);
 cudaError_t launch_split64(const WideArgs& a, unsigned grid, cudaStream_t s);
 cudaError_t launch_join64(const WideArgs& a, unsigned grid, cudaStream_t s);
 
+// The MSD plan's bucketing (msd.cu): bucket = order-mapped key >> kMsdShift
+// (2^14 buckets); C chunks of ceil(n / C) keys, one block each.
+constexpr uint32_t kMsdShift = 18;
+struct MsdArgs {
+  const uint32_t* keys;
+  uint64_t n;
+  KeyXform x;
+  uint32_t chunks;
+  uint32_t* hist;     // [chunks][2^14]: counts, then exclusive down each bucket's column
+  uint32_t* totals;   // [2^14]: bucket totals, then bucket bases
+  uint64_t* seg_off;  // [2^14 + 1]: bucket bases as segment offsets (last = n)
+  uint32_t* out;      // [n] bucketed, order-mapped keys (keys-only distribution)
+  uint32_t* err;      // device error word
+};
+size_t msd_smem();
+const void* msd_count_func();
+const void* msd_scatter_func();
+cudaError_t launch_msd_count(const MsdArgs& a, cudaStream_t s);
+cudaError_t launch_msd_scan(const MsdArgs& a, cudaStream_t s);
+cudaError_t launch_msd_scatter(const MsdArgs& a, cudaStream_t s);
+
 // The selection of Sec. 4.2.1 (select.cu): an evenly spaced sample of at
 // most 1024 keys, bucketed by the top `bits` of its significant width;
 // out[0] = problem cells, out[1] = 1 if more than max_problem, out[2] = the

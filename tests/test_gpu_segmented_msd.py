@@ -2,9 +2,10 @@
 (bit-exact).  Segments of every class are mixed in one call: empty, single
 keys, tiny (<= 4096 keys, one 256-thread block), small (<= 16384, one
 1024-thread block) and large (tiled passes whose lookback stays inside the
-segment).  The MSD plan buckets by the top byte (one tiled pass), then sorts
-every bucket through the same segmented pipeline (Sec. 3 / Sec. 4.6: bucketing,
-then a local radix sort per bucket)."""
+segment).  The MSD plan buckets by the keys' bits 18-31 (2^14 buckets; keys
+only: one counting read and one distribution pass; key+value: two stable
+passes), then sorts every bucket through the same segmented pipeline (Sec. 3 /
+Sec. 4.6: bucketing, then a local radix sort per bucket)."""
 import numpy as np
 import pytest
 
@@ -99,8 +100,54 @@ def test_msd_plan_distributions(rs, dist):
     assert np.array_equal(to_host_u32(vo), wv)
 
 
+@pytest.mark.parametrize("dist", sorted(synth.DISTRIBUTIONS))
+def test_msd_plan_full_size_distributions(rs, dist):
+    """The MSD plan at the workload size, 2^26 keys, keys only and with
+    payload = input position, for every distribution (tight clusters put
+    each cluster in one oversized bucket, sorted by tiled passes)."""
+    import torch
+    n = 1 << 26
+    keys = synth.config_keys(3, dist=dist) if dist != "uniform" else synth.config_keys(2)
+    plan = {"digit_bits": 8, "mode": rs.RS_MODE_MSD}
+    d = to_dev(keys)
+    ko, offs = rs.sort(d, plan=plan)
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk = oracle.sort_keys(keys)
+    assert np.array_equal(to_host_u32(ko), wk)
+    assert np.array_equal(offs, oracle.partition_offsets(n, 64))
+    del ko
+    vals = np.arange(n, dtype=np.uint32)
+    ko, vo, _ = rs.sort_pairs(d, to_dev(vals), plan=plan)
+    torch.cuda.synchronize()
+    rs.rs_check_device_error()
+    wk2, wv = oracle.sort_pairs(keys, vals)
+    assert np.array_equal(to_host_u32(ko), wk2)
+    assert np.array_equal(to_host_u32(vo), wv)
+
+
+def test_msd_bucket_boundaries(rs):
+    """Keys on both sides of every bucket boundary (bit 18), the lowest and
+    the highest bucket, and signed keys (the bucket is taken on the order map)."""
+    import torch
+    b = np.arange(0, 1 << 14, 37, dtype=np.uint64) << np.uint64(18)
+    bi = b.astype(np.int64)
+    keys = np.concatenate([bi, bi - 1, bi + 1, [0, 1, 0xFFFFFFFF, 0xFFFC0000]]) & 0xFFFFFFFF
+    keys = np.tile(keys.astype(np.uint32), 9)
+    for kind, code in (("u32", 0), ("i32", 1)):
+        plan = {"digit_bits": 8, "mode": rs.RS_MODE_MSD, "key_kind": code}
+        ko, _ = rs.sort(to_dev(keys), plan=plan)
+        vals = np.arange(keys.size, dtype=np.uint32)
+        ko2, vo2, _ = rs.sort_pairs(to_dev(keys), to_dev(vals), plan=plan)
+        torch.cuda.synchronize()
+        rs.rs_check_device_error()
+        assert np.array_equal(to_host_u32(ko), oracle.sort_keys(keys, kind))
+        wk, wv = oracle.sort_pairs(keys, vals, kind)
+        assert np.array_equal(to_host_u32(ko2), wk) and np.array_equal(to_host_u32(vo2), wv)
+
+
 def test_msd_skewed_top_byte(rs):
-    """All keys share the top byte: one bucket holds everything and goes
+    """All keys share the top byte: a few buckets hold everything and go
     through the tiled passes."""
     import torch
     n = 300_000
