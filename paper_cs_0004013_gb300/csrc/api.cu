@@ -58,6 +58,7 @@ struct DeviceState {
   uint32_t* err = nullptr;
   uint32_t* err_taken = nullptr;
   int num_sms = 0;
+  uint32_t fused_tiles[2] = {0, 0};  // tiles the single-launch sort can hold resident (keys, pairs)
 };
 std::mutex g_mu;
 std::mutex g_err_mu;  // one error-word check at a time (they share the copy word)
@@ -90,6 +91,17 @@ rs_status device_state(DeviceState** out) {
     for (const void* f : {msd_count_func(), msd_scatter_func()})
       RS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(msd_smem())),
               "cudaFuncSetAttribute(msd)");
+    int coop = 0;
+    RS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "cudaDeviceGetAttribute(coop)");
+    for (int pr = 0; pr < 2; ++pr) {
+      RS_CUDA(cudaFuncSetAttribute(fused_func(pr != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   int(fused_smem(pr != 0))),
+              "cudaFuncSetAttribute(fused)");
+      int per_sm = 0;
+      RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_func(pr != 0), 384, fused_smem(pr != 0)),
+              "cudaOccupancyMaxActiveBlocksPerMultiprocessor(fused)");
+      st.fused_tiles[pr] = coop ? uint32_t(per_sm) * uint32_t(st.num_sms) : 0u;
+    }
     const SegKernels* sk = seg_kernels();
     const void* fn[10] = {sk->pass_keys[0], sk->pass_pairs[0], sk->pass_keys[1], sk->pass_pairs[1],
                           sk->tiny_keys,    sk->tiny_pairs,    sk->small_keys,   sk->small_pairs,
@@ -110,13 +122,14 @@ rs_status device_state(DeviceState** out) {
 // ---- tracing -------------------------------------------------------------------
 enum TraceKind {
   T_CLEAR = 0, T_HIST, T_SCAN, T_PASS8, T_PASS11, T_SEGOFF, T_SEGPLAN, T_SEGHIST, T_SEGSCAN, T_SEGPASS, T_LOCAL,
-  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_MERGE, T_SELECT, T_MSDCOUNT, T_MSDSCAN, T_MSDSCATTER, T_KINDS
+  T_H2D, T_D2H, T_SPLIT, T_JOIN, T_MERGE, T_SELECT, T_MSDCOUNT, T_MSDSCAN, T_MSDSCATTER, T_FUSED, T_KINDS
 };
 const char* const kTraceNames[T_KINDS] = {"clear",       "upfront_hist", "digit_scan", "onesweep_r8",
                                           "onesweep_r11", "seg_part_offsets", "seg_plan", "seg_hist",
                                           "seg_scan",    "seg_pass",     "local_sort", "copy_h2d",
                                           "copy_d2h",    "split64",      "join64",     "merge",
-                                          "select",      "msd_count",    "msd_scan",   "msd_scatter"};
+                                          "select",      "msd_count",    "msd_scan",   "msd_scatter",
+                                          "fused_sort"};
 
 // The selection of Sec. 4.2.1 with the paper's parameters: a 1000-point
 // sample (footnote 8), 64 cells, 65 % overlap, more than two problem cells;
@@ -676,6 +689,37 @@ rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in
   return run_segmented(M.seg, temp, bk, bv, keys_out, vals_out, ma.seg_off, kMsdBuckets, 3, p.xf, p.xf, ds, s);
 }
 
+// ---- the single-launch sort -----------------------------------------------------
+// Up to (resident blocks) x 9,216 keys with the automatic plan: clear + one
+// cooperative launch instead of clear + histogram + scans + four passes.  It
+// uses the LSD layout's control words (word 12: the barrier counter), digit
+// histograms, status rows (its tiles are larger than the 512 x 16 tiles the
+// layout is sized for) and alternate buffers.
+rs_status run_fused(const SortPlan& p, const Layout& L, const uint32_t* keys_in, const uint32_t* vals_in,
+                    uint32_t* keys_out, uint32_t* vals_out, uint32_t n, unsigned char* temp, DeviceState* ds,
+                    cudaStream_t s) {
+  const bool pairs = vals_in != nullptr;
+  const uint32_t tiles = (n + fused_tile_keys() - 1) / fused_tile_keys();
+  if (size_t(tiles) * 256 * 4 > L.status_bytes) return fail(RS_ERR_CUDA, "single-launch sort: status too small");
+  RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, L.status + size_t(tiles) * 256 * 4, s); }),
+          "cudaMemsetAsync(temp)");
+  FusedArgs a{};
+  a.keys_in = keys_in;
+  a.keys_out = keys_out;
+  a.keys_alt = L.alt_k ? reinterpret_cast<uint32_t*>(temp + L.alt_k) : keys_out;
+  a.vals_in = vals_in;
+  a.vals_out = vals_out;
+  a.vals_alt = pairs && L.alt_v ? reinterpret_cast<uint32_t*>(temp + L.alt_v) : vals_out;
+  a.n = n;
+  a.xf = p.xf;
+  a.hist = reinterpret_cast<uint32_t*>(temp + L.hist);
+  a.status = temp + L.status;
+  a.bar = reinterpret_cast<uint32_t*>(temp + L.ctrl) + 12;
+  a.err = ds->err;
+  RS_CUDA(traced(T_FUSED, n, s, [&] { return launch_fused(a, tiles, pairs, s); }), "launch fused sort");
+  return RS_OK;
+}
+
 rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* keys_out, uint32_t* vals_out,
                     uint64_t n, uint32_t num_parts, uint64_t* h_part_offsets, const rs_plan* user_plan, void* temp,
                     size_t* temp_bytes, cudaStream_t s, bool pairs) {
@@ -746,6 +790,13 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
             "launch local_sort (one array)");
     return RS_OK;
   }
+  // Up to a few million keys: every tile resident at once, the whole sort in
+  // one launch (8-bit digits, the same passes).
+  if (automatic && p.R == 8 && p.nd == 4 && !p.k->wide_status &&
+      (n + fused_tile_keys() - 1) / fused_tile_keys() <= ds->fused_tiles[pairs ? 1 : 0] &&
+      size_t((n + fused_tile_keys() - 1) / fused_tile_keys()) * 1024 <= L.status_bytes)
+    return run_fused(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
+                     static_cast<unsigned char*>(temp), ds, s);
   return run_lsd(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
                  static_cast<unsigned char*>(temp), false, ds, s);
 }

@@ -110,48 +110,66 @@ __device__ __forceinline__ uint32_t scan256_exclusive(uint32_t x, uint32_t* s_sc
   return before + inc - x;
 }
 
-template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB>
-__global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs a) {
+// Where one tile of a pass comes from and goes to (the pass kernel fills it
+// from its launch arguments and its ticket; the single-launch sort from its
+// own plan of passes).
+struct Tile2Job {
+  uint32_t tile;         // tile index (row of the status array)
+  uint32_t n;            // keys of the pass
+  const uint32_t* kin;
+  uint32_t* kout;
+  const uint32_t* vin;   // payloads (NV >= 1)
+  uint32_t* vout;
+  KeyXform xin, xout;    // applied on load / inverted on store
+  uint32_t parity;       // status parity of this pass
+  void* status;          // [tiles][256] status words
+  const uint32_t* bases; // [256] keys with a smaller digit (global or shared memory)
+  uint32_t shift;        // the digit is byte shift / 8 of the key
+  uint32_t* err;         // device error word
+};
+
+// A key or payload load: read-only path for pass kernels; coherent (L2) in
+// the single-launch sort, whose later passes read what other blocks of the
+// same launch wrote.
+template <bool COHERENT>
+__device__ __forceinline__ uint32_t ld_pass(const uint32_t* p) {
+  if constexpr (COHERENT) {
+    uint32_t v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+  } else {
+    return ld_stream(p);
+  }
+}
+
+// Steps 1-6 for one tile.  The rank words must be zero and the block
+// synchronised on entry; the block is synchronised on return.
+template <int THREADS, int ITEMS, int NV, typename S, bool EARLY_LB, int LB, bool COHERENT>
+__device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned char* smem) {
   using L = Onesweep2Layout<THREADS, ITEMS, NV>;
   constexpr int DIGITS = L::DIGITS, GROUPS = L::GROUPS, TILE = L::TILE;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const Route route = route_of(a.skip, a.pass, a.num_passes);
-  if (!route.active) return;
-  const uint32_t* kin = route.src == BUF_IN ? a.keys_in : (route.src == BUF_OUT ? a.keys_out : a.keys_alt);
-  uint32_t* kout = route.dst == BUF_OUT ? a.keys_out : a.keys_alt;
-  const uint32_t* vin = nullptr;
-  uint32_t* vout = nullptr;
-  if constexpr (NV >= 1) {
-    vin = route.src == BUF_IN ? a.vals_in : (route.src == BUF_OUT ? a.vals_out : a.vals_alt);
-    vout = route.dst == BUF_OUT ? a.vals_out : a.vals_alt;
-  }
-  const KeyXform xin = route.src == BUF_IN ? a.xin : KeyXform{0u, 0u};
-  const KeyXform xout = route.last ? a.xout : KeyXform{0u, 0u};
-  const uint32_t parity = route.parity;
-  S* status = reinterpret_cast<S*>(a.status);
-
   uint32_t* s_key = reinterpret_cast<uint32_t*>(smem);
   uint32_t* s_val = reinterpret_cast<uint32_t*>(smem + L::KBUF);
   uint32_t* s_tbl = reinterpret_cast<uint32_t*>(smem + L::OFF_TBL);
   uint32_t* s_goff = reinterpret_cast<uint32_t*>(smem + L::OFF_GOFF);
   uint32_t* s_scan = reinterpret_cast<uint32_t*>(smem + L::OFF_SCAN);
-  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int l16 = lane & 15, grp = warp * 2 + (lane >> 4);
-
-  // 0. clear the rank words, take the tile ticket
-  {
-    uint4* t4 = reinterpret_cast<uint4*>(s_tbl);
-#pragma unroll 4
-    for (int i = tid; i < int(L::TBL / 16); i += THREADS) t4[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (tid == 0) *s_tile = atomicAdd(a.tile_counter, 1u);
-  }
-  __syncthreads();
-  const uint32_t tile = *s_tile;
+  const uint32_t tile = job.tile;
+  const uint32_t* kin = job.kin;
+  uint32_t* kout = job.kout;
+  const uint32_t* vin = job.vin;
+  uint32_t* vout = job.vout;
+  const KeyXform xin = job.xin, xout = job.xout;
+  const uint32_t parity = job.parity;
+  S* status = reinterpret_cast<S*>(job.status);
   const size_t tbase = size_t(tile) * TILE;
-  const size_t left = size_t(a.n) - tbase;
+  const size_t left = size_t(job.n) - tbase;
   const uint32_t valid = left < size_t(TILE) ? uint32_t(left) : uint32_t(TILE);
-  const uint32_t sel = 0x4440u | (a.shift >> 3);
+  const uint32_t sel = 0x4440u | (job.shift >> 3);
+  (void)vin;
+  (void)vout;
+  (void)s_val;
 
   // 1. load: group grp takes keys [grp * GKEYS, (grp + 1) * GKEYS) of the
   // tile, item j of lane l16 being key grp * GKEYS + j * 16 + l16.  Keys
@@ -162,7 +180,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs
   const uint32_t goff_in = uint32_t(grp) * L::GKEYS + uint32_t(l16);
   if (valid == TILE) {
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j) key[j] = ld_stream(kin + tbase + goff_in + j * 16);
+    for (int j = 0; j < ITEMS; ++j) key[j] = ld_pass<COHERENT>(kin + tbase + goff_in + j * 16);
     if (!is_identity(xin)) {
 #pragma unroll
       for (int j = 0; j < ITEMS; ++j) key[j] = to_ordered(key[j], xin);
@@ -171,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const uint32_t i = goff_in + j * 16;
-      key[j] = i < valid ? to_ordered(kin[tbase + i], xin) : 0xffffffffu;
+      key[j] = i < valid ? to_ordered(ld_pass<COHERENT>(kin + tbase + i), xin) : 0xffffffffu;
     }
   }
 
@@ -208,9 +226,9 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs
   auto do_lookback = [&]() {
     if (tid < DIGITS) {
       uint32_t prefix[1];
-      lookback<DIGITS, 1, S, LB>(status, tile, 0u, tid, parity, a.err, prefix);
+      lookback<DIGITS, 1, S, LB>(status, tile, 0u, tid, parity, job.err, prefix);
       if (tile != 0) st_relaxed(status + size_t(tile) * DIGITS + tid, status_word<S>(parity, true, prefix[0] + tot));
-      s_goff[tid] = a.bases[tid] + prefix[0] - excl;
+      s_goff[tid] = job.bases[tid] + prefix[0] - excl;
     }
   };
   if constexpr (EARLY_LB) do_lookback();
@@ -244,12 +262,12 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs
     uint32_t val[ITEMS];
     if (valid == TILE) {
 #pragma unroll
-      for (int j = 0; j < ITEMS; ++j) val[j] = ld_stream(vin + tbase + goff_in + j * 16);
+      for (int j = 0; j < ITEMS; ++j) val[j] = ld_pass<COHERENT>(vin + tbase + goff_in + j * 16);
     } else {
 #pragma unroll
       for (int j = 0; j < ITEMS; ++j) {
         const uint32_t i = goff_in + j * 16;
-        val[j] = i < valid ? vin[tbase + i] : 0u;
+        val[j] = i < valid ? ld_pass<COHERENT>(vin + tbase + i) : 0u;
       }
     }
 #pragma unroll
@@ -266,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs
   // check only guards against a corrupted offset (it raises an error bit
   // instead of writing out of bounds).
   bool oob = false;
-  const uint32_t n = a.n;
+  const uint32_t n = job.n;
   const uint32_t sg = smem_addr(s_goff);
   auto write_out = [&](auto invert) {
     constexpr int B = ITEMS % 8 == 0 ? 8 : (ITEMS % 6 == 0 ? 6 : (ITEMS % 4 == 0 ? 4 : 1));
@@ -293,7 +311,45 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs
   };
   if (is_identity(xout)) write_out(std::false_type{});
   else write_out(std::true_type{});
-  if (oob) atomicOr(a.err, kErrBounds);
+  if (oob) atomicOr(job.err, kErrBounds);
+  __syncthreads();
+}
+
+
+template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB>
+__global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs a) {
+  using L = Onesweep2Layout<THREADS, ITEMS, NV>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const Route route = route_of(a.skip, a.pass, a.num_passes);
+  if (!route.active) return;
+  Tile2Job job;
+  job.kin = route.src == BUF_IN ? a.keys_in : (route.src == BUF_OUT ? a.keys_out : a.keys_alt);
+  job.kout = route.dst == BUF_OUT ? a.keys_out : a.keys_alt;
+  job.vin = nullptr;
+  job.vout = nullptr;
+  if constexpr (NV >= 1) {
+    job.vin = route.src == BUF_IN ? a.vals_in : (route.src == BUF_OUT ? a.vals_out : a.vals_alt);
+    job.vout = route.dst == BUF_OUT ? a.vals_out : a.vals_alt;
+  }
+  job.xin = route.src == BUF_IN ? a.xin : KeyXform{0u, 0u};
+  job.xout = route.last ? a.xout : KeyXform{0u, 0u};
+  job.parity = route.parity;
+  job.status = a.status;
+  job.bases = a.bases;
+  job.shift = a.shift;
+  job.err = a.err;
+  job.n = a.n;
+  // 0. clear the rank words, take the tile ticket
+  uint32_t* s_tile = reinterpret_cast<uint32_t*>(smem + L::OFF_TILE);
+  {
+    uint4* t4 = reinterpret_cast<uint4*>(smem + L::OFF_TBL);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < int(L::TBL / 16); i += THREADS) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x == 0) *s_tile = atomicAdd(a.tile_counter, 1u);
+  }
+  __syncthreads();
+  job.tile = *s_tile;
+  onesweep2_tile<THREADS, ITEMS, NV, S, EARLY_LB, LB, false>(job, smem);
 }
 
 template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB>

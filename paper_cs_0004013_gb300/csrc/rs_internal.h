@@ -273,6 +273,27 @@ cudaError_t launch_merge(const MergeArgs& m, cudaStream_t s);
 cudaError_t launch_split64(const WideArgs& a, unsigned grid, cudaStream_t s);
 cudaError_t launch_join64(const WideArgs& a, unsigned grid, cudaStream_t s);
 
+// A whole sort of up to a few million keys in one cooperative launch
+// (fused.cu): 8-bit digits, one 384 x 24 tile per block, every block resident.
+struct FusedArgs {
+  const uint32_t* keys_in;
+  uint32_t* keys_out;
+  uint32_t* keys_alt;
+  const uint32_t* vals_in;   // null for keys only
+  uint32_t* vals_out;
+  uint32_t* vals_alt;
+  uint32_t n;
+  KeyXform xf;               // order map of the keys' kind
+  uint32_t* hist;            // [4][256], zero on entry
+  void* status;              // [tiles][256] 32-bit status words, zero on entry
+  uint32_t* bar;             // barrier counter, zero on entry
+  uint32_t* err;             // device error word
+};
+uint32_t fused_tile_keys();
+size_t fused_smem(bool pairs);
+const void* fused_func(bool pairs);
+cudaError_t launch_fused(const FusedArgs& a, unsigned tiles, bool pairs, cudaStream_t s);
+
 // The MSD plan's bucketing (msd.cu): bucket = order-mapped key >> kMsdShift
 // (2^14 buckets); C chunks of ceil(n / C) keys, one block each.
 constexpr uint32_t kMsdShift = 18;
