@@ -28,7 +28,7 @@ def _segments(seed, count=60, lo=2000, hi=16000):
 def test_installed_plain_plan_is_the_one_that_runs(rs):
     """An 11-bit plan installed for the 2^20 class: a call without a plan
     runs 11-bit passes (trace), keys and pairs match the oracle; removing
-    the entry brings back the compiled default (8-bit passes)."""
+    the entry brings back the compiled default (8-bit passes, in one launch)."""
     import torch
     n = (1 << 20) - 3  # class 20
     keys = synth.gauss_mix(n, 41)
@@ -57,7 +57,8 @@ def test_installed_plain_plan_is_the_one_that_runs(rs):
     torch.cuda.synchronize()
     rs.rs_trace_enable(False)
     tr = rs.rs_trace_read()
-    assert "onesweep_r8" in tr and "onesweep_r11" not in tr
+    # the compiled default at this size: the single-launch sort (8-bit passes)
+    assert "onesweep_r11" not in tr and ("fused_sort" in tr or "onesweep_r8" in tr)
     assert np.array_equal(to_host_u32(out), oracle.sort_keys(keys))
 
 
