@@ -78,9 +78,14 @@ rs_status device_state(DeviceState** out) {
     int cnt = 0;
     for (int r : {8, 11}) {
       const OnesweepKernel* ks = r == 8 ? onesweep_kernels_r8(&cnt) : onesweep_kernels_r11(&cnt);
-      for (int i = 0; i < cnt; ++i)
+      for (int i = 0; i < cnt; ++i) {
         RS_CUDA(cudaFuncSetAttribute(ks[i].func, cudaFuncAttributeMaxDynamicSharedMemorySize, int(ks[i].smem)),
                 "cudaFuncSetAttribute(onesweep)");
+        if (ks[i].func_first)
+          RS_CUDA(cudaFuncSetAttribute(ks[i].func_first, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(ks[i].smem)),
+                  "cudaFuncSetAttribute(onesweep first pass)");
+      }
       const HistKernel* h = hist_kernel(r);
       for (const void* f : h->funcs)
         if (f)
@@ -439,7 +444,10 @@ rs_status run_lsd(const SortPlan& p, const Layout& L, const uint32_t* keys_in, c
     pa.xout = p.xf;  // the last one maps them back
     pa.pair_in = pair_vals_in;  // 64-bit values read and written interleaved
     pa.pair_out = pair_vals_out;
-    RS_CUDA(traced(p.R == 8 ? T_PASS8 : T_PASS11, n, s, [&] { return p.k->launch(pa, pass_grid(p, ds), s); }),
+    // pass 0, when it runs, is the first executed pass: keys-only sorts rank it
+    // without keeping the order of equal digits (there is none to keep yet)
+    auto launch = (j == 0 && p.k->launch_first && !vals_in) ? p.k->launch_first : p.k->launch;
+    RS_CUDA(traced(p.R == 8 ? T_PASS8 : T_PASS11, n, s, [&] { return launch(pa, pass_grid(p, ds), s); }),
             "launch onesweep");
   }
   return RS_OK;

@@ -145,7 +145,12 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks) fused_sort_ker
     job.bases = s_bases + 256 * j;
     job.shift = uint32_t(8 * j);
     job.err = a.err;
-    onesweep2_tile<kFusedThreads, kFusedItems, NV, uint32_t, false, kFusedLookback, true>(job, smem);
+    bool unstable = false;  // the first executed pass of keys on a full tile: equal digits leave in any order
+    if constexpr (NV == 0) unstable = e == 0 && (size_t(tile) + 1) * L::TILE <= size_t(n);
+    if (unstable)
+      onesweep2_tile<kFusedThreads, kFusedItems, NV, uint32_t, false, kFusedLookback, true, true>(job, smem);
+    else
+      onesweep2_tile<kFusedThreads, kFusedItems, NV, uint32_t, false, kFusedLookback, true, false>(job, smem);
     if (e + 1 < m) grid_barrier(a.bar, tiles * uint32_t(2 + e), a.err);
   }
 }

@@ -144,7 +144,8 @@ __device__ __forceinline__ uint32_t ld_pass(const uint32_t* p) {
 
 // Steps 1-6 for one tile.  The rank words must be zero and the block
 // synchronised on entry; the block is synchronised on return.
-template <int THREADS, int ITEMS, int NV, typename S, bool EARLY_LB, int LB, bool COHERENT>
+// UNSTABLE (keys only): the first executed pass, see step 2u.
+template <int THREADS, int ITEMS, int NV, typename S, bool EARLY_LB, int LB, bool COHERENT, bool UNSTABLE = false>
 __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned char* smem) {
   using L = Onesweep2Layout<THREADS, ITEMS, NV>;
   constexpr int DIGITS = L::DIGITS, GROUPS = L::GROUPS, TILE = L::TILE;
@@ -165,7 +166,10 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
   S* status = reinterpret_cast<S*>(job.status);
   const size_t tbase = size_t(tile) * TILE;
   const size_t left = size_t(job.n) - tbase;
-  const uint32_t valid = left < size_t(TILE) ? uint32_t(left) : uint32_t(TILE);
+  // UNSTABLE runs on full tiles only: keys past the end would take places
+  // among the tile's real keys of digit 255 (the atomic ranking keeps no
+  // order), so the caller gives a partial tile to the stable body
+  const uint32_t valid = (NV == 0 && UNSTABLE) || left >= size_t(TILE) ? uint32_t(TILE) : uint32_t(left);
   const uint32_t sel = 0x4440u | (job.shift >> 3);
   (void)vin;
   (void)vout;
@@ -193,8 +197,16 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
     }
   }
 
-  // 2. early counts per (group, digit)
-  const uint32_t tb_grp = smem_addr(s_tbl + grp * DIGITS);
+  // Keys only, first executed pass of a full tile (UNSTABLE): the order of
+  // keys with the same lowest digit is free (there is no earlier order to
+  // keep, and keys with equal digits here are told apart by the later passes
+  // or are equal), so one shared counter per digit for the whole tile
+  // suffices and a key's position is one atomic add on it (steps 2u and 4u
+  // below) instead of the groups' mask words.
+  constexpr bool unstable = NV == 0 && UNSTABLE;
+
+  // 2. early counts per (group, digit) [2u: per digit]
+  const uint32_t tb_grp = smem_addr(s_tbl + (unstable ? 0 : grp * DIGITS));
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) sh_red_add(tb_grp + 4u * byte_digit(key[j], sel), 1u);
   __syncthreads();
@@ -202,19 +214,27 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
   // 3. per digit (threads 0..255): the tile's count -> aggregate status now;
   // exclusive scan over digits -> where each digit's run starts in the
   // staged tile; then each group's counter -> the position of its first key
-  // of the digit
+  // of the digit [3u: the digit's counter -> the start of its run]
   uint32_t tot = 0, excl = 0;
   if (tid < DIGITS) {
+    if constexpr (unstable) {
+      tot = s_tbl[tid];
+    } else {
 #pragma unroll 8
-    for (int g = 0; g < GROUPS; ++g) tot += s_tbl[g * DIGITS + tid];
+      for (int g = 0; g < GROUPS; ++g) tot += s_tbl[g * DIGITS + tid];
+    }
     st_relaxed(status + size_t(tile) * DIGITS + tid, status_word<S>(parity, tile == 0, tot));
     excl = scan256_exclusive(tot, s_scan);
-    uint32_t run = excl;
+    if constexpr (unstable) {
+      s_tbl[tid] = excl;
+    } else {
+      uint32_t run = excl;
 #pragma unroll 8
-    for (int g = 0; g < GROUPS; ++g) {
-      const uint32_t c = s_tbl[g * DIGITS + tid];
-      s_tbl[g * DIGITS + tid] = run;
-      run += c;
+      for (int g = 0; g < GROUPS; ++g) {
+        const uint32_t c = s_tbl[g * DIGITS + tid];
+        s_tbl[g * DIGITS + tid] = run;
+        run += c;
+      }
     }
   }
   __syncthreads();
@@ -238,20 +258,30 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
   const uint32_t mybit = 1u << (16 + l16);
   const uint32_t sk = smem_addr(s_key);
   uint32_t pos[NV >= 1 ? (ITEMS + 1) / 2 : 1];
+  if constexpr (unstable) {
+    // 4u. one atomic add per key on its digit's counter gives its place
 #pragma unroll
-  for (int j = 0; j < ITEMS; ++j) {
-    const uint32_t ad = tb_grp + 4u * byte_digit(key[j], sel);
-    sh_red_or(ad, mybit);
-    __syncwarp();
-    const uint32_t v = sh_ld(ad);
-    const uint32_t peers = v >> 16, base = v & 0xffffu;
-    const uint32_t p = base + __popc(peers & lt16);
-    if ((peers >> l16) == 1u) sh_st(ad, base + __popc(peers));  // the group's highest lane with this digit
-    __syncwarp();
-    sh_st(sk + 4u * p, key[j]);
-    if constexpr (NV >= 1) {
-      if (j & 1) pos[j >> 1] |= p << 16;
-      else pos[j >> 1] = p;
+    for (int j = 0; j < ITEMS; ++j) {
+      uint32_t p;
+      asm volatile("atom.shared.add.u32 %0, [%1], 1;" : "=r"(p) : "r"(tb_grp + 4u * byte_digit(key[j], sel)) : "memory");
+      sh_st(sk + 4u * p, key[j]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const uint32_t ad = tb_grp + 4u * byte_digit(key[j], sel);
+      sh_red_or(ad, mybit);
+      __syncwarp();
+      const uint32_t v = sh_ld(ad);
+      const uint32_t peers = v >> 16, base = v & 0xffffu;
+      const uint32_t p = base + __popc(peers & lt16);
+      if ((peers >> l16) == 1u) sh_st(ad, base + __popc(peers));  // the group's highest lane with this digit
+      __syncwarp();
+      sh_st(sk + 4u * p, key[j]);
+      if constexpr (NV >= 1) {
+        if (j & 1) pos[j >> 1] |= p << 16;
+        else pos[j >> 1] = p;
+      }
     }
   }
   if constexpr (!EARLY_LB) do_lookback();
@@ -316,7 +346,7 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
 }
 
 
-template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB>
+template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB, bool UNSTABLE>
 __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs a) {
   using L = Onesweep2Layout<THREADS, ITEMS, NV>;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -349,13 +379,20 @@ __global__ void __launch_bounds__(THREADS, MINB) onesweep2_kernel(const PassArgs
   }
   __syncthreads();
   job.tile = *s_tile;
-  onesweep2_tile<THREADS, ITEMS, NV, S, EARLY_LB, LB, false>(job, smem);
+  if constexpr (UNSTABLE) {
+    // the first executed pass of this sort, on a full tile
+    if (route.src == BUF_IN && (size_t(job.tile) + 1) * L::TILE <= size_t(a.n)) {
+      onesweep2_tile<THREADS, ITEMS, NV, S, EARLY_LB, LB, false, true>(job, smem);
+      return;
+    }
+  }
+  onesweep2_tile<THREADS, ITEMS, NV, S, EARLY_LB, LB, false, false>(job, smem);
 }
 
-template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB>
+template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB, int LB, bool UNSTABLE>
 cudaError_t launch_onesweep2(const PassArgs& a, unsigned grid, cudaStream_t s) {
   using L = Onesweep2Layout<THREADS, ITEMS, NV>;
-  onesweep2_kernel<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB><<<grid, THREADS, L::SMEM, s>>>(a);
+  onesweep2_kernel<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB, UNSTABLE><<<grid, THREADS, L::SMEM, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -364,6 +401,12 @@ cudaError_t launch_onesweep2(const PassArgs& a, unsigned grid, cudaStream_t s) {
 template <int THREADS, int ITEMS, int NV, typename S, int MINB, bool EARLY_LB = false, int LB = 8>
 OnesweepKernel make_onesweep2(int shape_id) {
   using L = Onesweep2Layout<THREADS, ITEMS, NV>;
+  cudaError_t (*first)(const PassArgs&, unsigned, cudaStream_t) = nullptr;
+  const void* first_func = nullptr;
+  if constexpr (NV == 0) {
+    first = &launch_onesweep2<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB, true>;
+    first_func = reinterpret_cast<const void*>(&onesweep2_kernel<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB, true>);
+  }
   return OnesweepKernel{8,
                         shape_id,
                         THREADS,
@@ -372,11 +415,13 @@ OnesweepKernel make_onesweep2(int shape_id) {
                         NV >= 1,
                         sizeof(S) == 8,
                         L::SMEM,
-                        &launch_onesweep2<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB>,
-                        reinterpret_cast<const void*>(&onesweep2_kernel<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB>),
+                        &launch_onesweep2<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB, false>,
+                        reinterpret_cast<const void*>(&onesweep2_kernel<THREADS, ITEMS, NV, S, MINB, EARLY_LB, LB, false>),
                         0,
                         NV,
-                        false};
+                        false,
+                        first,
+                        first_func};
 }
 
 }  // namespace rs

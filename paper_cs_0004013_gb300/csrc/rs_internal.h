@@ -124,6 +124,10 @@ struct OnesweepKernel {
   int persistent_per_sm = 0;  // > 0: persistent kernel, grid = SMs x this (capped by tiles)
   int value_words = -1;       // payload words per key (-1: 1 if pairs else 0)
   bool pair_io = false;       // reads and writes interleaved 64-bit words (PassArgs pair_* and gather fields)
+  // Keys only: the kernel for pass 0, which ranks without keeping the order of
+  // equal digits when it is the sort's first executed pass (null: `launch`).
+  cudaError_t (*launch_first)(const PassArgs&, unsigned grid, cudaStream_t) = nullptr;
+  const void* func_first = nullptr;
   int vwords() const { return value_words >= 0 ? value_words : (pairs ? 1 : 0); }
 };
 
