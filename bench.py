@@ -61,13 +61,14 @@ FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 126 * 1024 * 1024
 FLUSH_BYTES = 256 << 20
 E2E_STREAMS = 3
-CLOCK_SETTLE_S = 0.5
+CLOCK_SETTLE_S = 1.0
+REFERENCE_BUDGET_S = 100.0  # the reference arm's whole run
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=N_KEYS, help="keys per sort (default 2^26)")
@@ -110,7 +111,7 @@ def dist_env():
 
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples every 200 ms, each stamped with the host time it
+    """nvidia-smi samples every 100 ms, each stamped with the host time it
     arrived, so that the samples of a time window can be picked out."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -126,7 +127,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
         if self.proc is not None:
@@ -234,23 +235,35 @@ def run_reference(args):
     import oracle
     import synth
     keys = synth.uniform31(N_KEYS, synth.CONFIG_SEED + 2)  # the workload itself
+    # Each step sorts a prefix of the workload's keys, as long as the whole
+    # run fits REFERENCE_BUDGET_S (the oracle takes seconds per 2^26 keys):
+    # the prefix is the longest power of two whose estimated time, scaled
+    # from one timed sort of 2^20 keys, fits the steps plus one warm-up.
+    t0 = time.perf_counter()
+    oracle.sort_keys(keys[: 1 << 20])
+    per_key = (time.perf_counter() - t0) / (1 << 20) * 1.3  # n log n growth up to 2^26
+    size = N_KEYS
+    while size > (1 << 20) and (args.steps + min(args.warmup, 1)) * size * per_key > REFERENCE_BUDGET_S:
+        size //= 2
+    sample = keys[:size]
     for _ in range(min(args.warmup, 1)):
-        oracle.sort_keys(keys)
+        oracle.sort_keys(sample)
     t = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sort_keys(keys)
+        oracle.sort_keys(sample)
         t.append(time.perf_counter() - t0)
     tot = sum(t)
-    rate = args.steps * keys.size / tot / 1e9
+    rate = args.steps * sample.size / tot / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "Gkeys/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "keys_per_step": int(keys.size)},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "keys_per_step": int(sample.size)},
             "cpu_baseline": {"value": rate, "unit": "Gkeys/s", "cores": 1, "host_cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": "each step sorts the whole workload: 2^26 uniform 31-bit keys "
-                                       "(numpy stable sort, one host thread); at most one warm-up sort"},
+                             "sample": f"each step sorts the first 2^{size.bit_length() - 1} of the workload's "
+                                       "2^26 uniform 31-bit keys (numpy stable sort, one host thread); "
+                                       "at most one warm-up sort"},
             "e2e": {"value": rate, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -391,8 +404,8 @@ def run_ours(args):
     flush_l2 = 4 * n * (3 if vals64 else 2 if pairs else 1) * 2 < L2_BYTES
     flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev) if flush_l2 else None
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # The clock record: nvidia-smi samples every 200 ms, and a timed region of
-    # tens of milliseconds may hold none.  So the sampler starts first, and
+    # The clock record: nvidia-smi samples every 100 ms, and a timed region of
+    # tens of milliseconds (a short --steps) may hold none.  So the sampler starts first, and
     # the same sort runs, untimed, for CLOCK_SETTLE_S before the timed steps;
     # the summary takes the samples from that start to the end of the traced
     # steps (all under this load) and counts those inside the timed region.
@@ -870,9 +883,10 @@ def measure_served(requests: int, rounds: int) -> dict:
 def run_serve(args):
     import torch
     torch.cuda.set_device(0)
-    sv = measure_served(args.requests, max(args.steps // 10, 1))
+    rounds = min(max(args.steps // 10, 1), 5)
+    sv = measure_served(args.requests, rounds)
     line = {"metric": METRIC, "value": sv["value"], "unit": "Gkeys/s", "n_gpus": 1,
-            "steps": max(args.steps // 10, 1), "warmup": 1, "ms_per_step": sv["seconds"] * 1e3,
+            "steps": rounds, "warmup": 1, "ms_per_step": sv["seconds"] * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": sv["workload"], "total_keys": sv["total_keys"]},
             **{k: sv[k] for k in ("serial_plain", "speedup_vs_serial", "load_points", "results_checked")}}
