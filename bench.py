@@ -563,14 +563,54 @@ def run_ours(args):
         piped = statistics.median(piped_runs)
         rs.rs_check_device_error()
         per_step = (8 if pairs else 4) * n
-        e2e = {"value": piped, "unit": "Gkeys/s", "h2d_bytes_per_step": per_step, "d2h_bytes_per_step": per_step,
-               "streams": E2E_STREAMS, "repeats": piped_runs, "one_stream_value": serial,
-               "api": "rs_sort_u32_host (pinned host buffers; copies of consecutive sorts overlap)"}
+
+        # The host link's own ceiling in this run: a step's copies in both
+        # directions at once (the same pinned buffers and byte counts, no
+        # sort), so that the end-to-end figure can be read against it.
+        def link_rate(reps=10):
+            src = [torch.zeros(n, dtype=torch.int32, device=dev) for _ in range(2 if pairs else 1)]
+            dst = [torch.zeros(n, dtype=torch.int32, device=dev) for _ in range(2 if pairs else 1)]
+            hin = [h_in] + ([h_vin] if pairs else [])
+            hout = [slots[0][1]] + ([slots[0][2]] if pairs else [])
+            cur = torch.cuda.current_stream()
+
+            def timed(k):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(cur)
+                for st in streams[:2]:
+                    st.wait_event(e0)
+                for _ in range(k):
+                    with torch.cuda.stream(streams[0]):
+                        for d, h in zip(dst, hin):
+                            d.copy_(h, non_blocking=True)
+                    with torch.cuda.stream(streams[1]):
+                        for h, d in zip(hout, src):
+                            h.copy_(d, non_blocking=True)
+                for st in streams[:2]:
+                    done = torch.cuda.Event()
+                    done.record(st)
+                    cur.wait_event(done)
+                e1.record(cur)
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1) / k
+
+            timed(3)  # warm-up
+            ms = min(timed(reps) for _ in range(2))
+            return {"value": n / ms / 1e6, "unit": "Gkeys/s", "ms_per_step": ms,
+                    "gb_per_s_both_directions": 2 * per_step / ms / 1e6}
+
         for tmp, h_out, h_vout in slots:
             ok = np.array_equal(h_out.numpy().view(np.uint32)[:: max(1, n // 4096)],
                                 sorted_by_kind(keys, args.key_kind)[:: max(1, n // 4096)])
             if not ok:
                 raise SystemExit("end-to-end output is not the sorted keys")
+        link = link_rate()  # after the check: it overwrites slot 0's host output
+        link["frac"] = piped / link["value"]
+        e2e = {"value": piped, "unit": "Gkeys/s", "h2d_bytes_per_step": per_step, "d2h_bytes_per_step": per_step,
+               "streams": E2E_STREAMS, "repeats": piped_runs, "one_stream_value": serial,
+               "api": "rs_sort_u32_host (pinned host buffers; copies of consecutive sorts overlap)",
+               "link_ceiling": link}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -842,9 +882,10 @@ def measure_served(requests: int, rounds: int) -> dict:
     t_serial = serial_plain(base)
     serial_rate = total_keys / t_serial / 1e9
     cap_req_s = len(base) / t_serial
-    # eight batches in flight on eight streams (24.6 Gkeys/s closed loop
-    # against 20.8 with four); results lent from a 16 GiB pinned pool
-    srv = SortServer(slots=8, streams=8, mem_budget=24 << 30, result_pool=ResultPool(16 << 30))
+    # sixteen batches in flight on sixteen streams (closed loop on GB300:
+    # 21.5-22.0 Gkeys/s against 19.4 with eight); results lent from a 16 GiB
+    # pinned pool
+    srv = SortServer(slots=16, streams=16, mem_budget=24 << 30, result_pool=ResultPool(16 << 30))
     srv.run(make(1e9, synth.CONFIG_SEED + 5)[:100], realtime=False)  # warm-up (pools, kernels)
     points = []
     for load in (0.5, 0.8, 1.2):

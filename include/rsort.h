@@ -363,6 +363,17 @@ const char* rs_last_error(void);
  * raised after this check's take is kept for the next one.                 */
 rs_status rs_check_device_error(rs_stream_t stream);
 
+/* Enqueues on `stream`, after its earlier work, a copy of the current
+ * device's error word into *h_word (HOST, 4 bytes; pinned memory keeps the
+ * copy asynchronous) without clearing it, and returns at once: no kernel,
+ * no wait.  *h_word is valid once the stream's later events complete.  A
+ * nonzero word says that some kernel of the device raised an error bit
+ * since the last rs_check_device_error() (which takes and clears it): bit 0
+ * (1) a bounded wait gave up, bit 1 (2) an output-index check fired.  Zero
+ * says that none had by the time of the copy.  Meant for callers that keep
+ * many streams busy and must not wait on each one.                        */
+rs_status rs_peek_device_error_async(uint32_t* h_word, rs_stream_t stream);
+
 /* ---- tracing ------------------------------------------------------------ */
 
 /* Per-kernel timing.  While enabled, every kernel the library launches is

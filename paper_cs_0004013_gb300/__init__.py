@@ -22,7 +22,7 @@ from .build import LIB as LIBRARY_PATH
 __all__ = [
     "RsError", "RsPlan", "lib", "LIBRARY_PATH",
     "rs_sort_u32", "rs_sort_u32_pairs", "rs_sort_u32_segmented", "rs_digit_histograms",
-    "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_version", "rs_trace_enable",
+    "rs_radix_pass", "rs_last_error", "rs_check_device_error", "rs_peek_device_error_async", "rs_version", "rs_trace_enable",
     "rs_trace_read", "rs_sort_u32_noalloc", "RS_NOALLOC_MAX_KEYS", "rs_selftest_wait_timeout",
     "rs_sort_u32_host", "rs_sort_u64", "sort64", "rs_sort_u64_pairs", "rs_sort_u64_pairs64", "sort64_pairs", "rs_sort_u32_pairs64", "sort_pairs64", "rs_merge_u32", "merge",
     "sort", "sort_pairs", "sort_segmented", "temp_bytes",
@@ -70,6 +70,7 @@ _SIGS = {
     "rs_radix_pass": [_P, _P, _P, _P, _U64, _U32, _U32, _P, _SZP, _P],
     "rs_last_error": [],
     "rs_check_device_error": [_P],
+    "rs_peek_device_error_async": [_P, _P],
     "rs_version": [],
     "rs_trace_enable": [ctypes.c_int],
     "rs_sort_u32_host": [_P, _P, _P, _P, _U64, _U32, _U64P, _PLANP, _P, _SZP, _P],
@@ -378,6 +379,14 @@ def rs_get_default_plan(entry: int, size_class: int):
 
 def rs_check_device_error(stream=None) -> None:
     _check(lib.rs_check_device_error(_stream(stream)))
+
+
+def rs_peek_device_error_async(h_word, stream=None) -> None:
+    """Enqueues a copy of the device error word into h_word (a pinned CPU
+    tensor of at least 4 bytes); see include/rsort.h."""
+    if h_word.device.type != "cpu" or h_word.numel() * h_word.element_size() < 4:
+        raise ValueError("h_word must be a CPU tensor of at least 4 bytes")
+    _check(lib.rs_peek_device_error_async(_ptr(h_word), _stream(stream)))
 
 
 def rs_selftest_wait_timeout(temp, stream=None) -> None:

@@ -1525,6 +1525,18 @@ rs_status rs_check_device_error(rs_stream_t stream) {
   return RS_OK;
 }
 
+rs_status rs_peek_device_error_async(uint32_t* h_word, rs_stream_t stream) {
+  g_last_error.clear();
+  if (!h_word) return fail(RS_ERR_INVALID, "h_word is NULL");
+  DeviceState* ds = nullptr;
+  rs_status st = device_state(&ds);
+  if (st != RS_OK) return st;
+  RS_CUDA(cudaMemcpyAsync(h_word, ds->err, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                          reinterpret_cast<cudaStream_t>(stream)),
+          "copy device error word");
+  return RS_OK;
+}
+
 rs_status rs_trace_enable(int on) {
   g_last_error.clear();
   std::lock_guard<std::mutex> lock(g_trace_mu);

@@ -5,8 +5,9 @@ each scheduler tick, the requests that have arrived are admitted while a slot
 is free and the device-memory budget allows; each admitted group becomes one
 batch: its requests are copied (pinned host -> device) into one arena, sorted
 by a single ``rs_sort_u32_segmented`` call (each request is one segment), and
-copied back (device -> pinned host), all on one of ``streams`` CUDA streams,
-so batches formed at different ticks overlap on the device.  A request of at
+copied back (device -> pinned host), all on one of ``streams`` CUDA streams
+(one that no batch in flight uses), so batches formed at different ticks
+overlap on the device.  A request of at
 least ``direct_min_keys`` keys forms a batch of its own, sorted by one
 ``rs_sort_u32_host`` call straight from and into its pinned buffers (the
 plain sort's kernels, no arena); one such batch's copy back then overlaps the
@@ -20,12 +21,14 @@ only; all sorting runs in librsort's kernels.  Each request's result does not
 depend on what it was batched with (the segmented sort treats every segment
 on its own), which ``tests/test_gpu_serve.py`` checks bit for bit.
 
-When a batch completes, the server takes the device error word (bounded
-waits that gave up, output-index checks that fired) on the batch's stream.
-The word is shared by every stream of the device, so an error cannot be
-pinned on one batch: the completed batch and every batch still in flight at
-that moment are marked failed (``Request.error``), and ``run`` returns with
-``failed`` counting them instead of reporting wrong results as served.
+After each batch's work its stream copies the device error word (bounded
+waits that gave up, output-index checks that fired) into a pinned word,
+asynchronously; when the batch completes, the server reads that copy, and
+only if a bit is set does it take and clear the word (on a stream of its
+own).  The word is shared by every stream of the device, so an error cannot
+be pinned on one batch: the completed batch and every batch still in flight
+at that moment are marked failed (``Request.error``), and ``run`` returns
+with ``failed`` counting them instead of reporting wrong results as served.
 """
 from __future__ import annotations
 
@@ -36,7 +39,8 @@ from collections import deque
 
 import numpy as np
 
-from . import RsError, rs_check_device_error, rs_sort_u32, rs_sort_u32_host, rs_sort_u32_pairs, rs_sort_u32_segmented
+from . import (RsError, rs_check_device_error, rs_peek_device_error_async, rs_sort_u32, rs_sort_u32_host,
+               rs_sort_u32_pairs, rs_sort_u32_segmented)
 
 __all__ = ["Request", "ResultPool", "SortServer", "serial_plain", "latency_stats"]
 
@@ -150,6 +154,11 @@ class _Batch:
         self.id, self.reqs, self.pairs, self.stream = bid, reqs, pairs, stream
         self.arena, self.temp, self.h_in, self.h_out = arena, temp, h_in, h_out
         self.done_event, self.start_event = done_event, start_event
+        self.err_word = None  # pinned copy of the device error word, taken after the batch's work
+
+
+# error-word bits (include/rsort.h, rs_peek_device_error_async)
+_ERR_TIMEOUT, _ERR_BOUNDS = 1, 2
 
 
 class SortServer:
@@ -177,6 +186,9 @@ class SortServer:
         self.direct_min_keys = direct_min_keys
         self.num_parts = num_parts
         self.streams = [torch.cuda.Stream(device=self.device) for _ in range(streams)]
+        # the error word is taken on a stream of its own (see _check_errors)
+        self.err_stream = torch.cuda.Stream(device=self.device)
+        self.err_words: list = []  # pinned 4-byte words for the per-batch peeks
         self.pool = _Pool(self.device)
         self.pinned = {}
         self.in_flight: list[_Batch] = []
@@ -207,16 +219,35 @@ class SortServer:
                                      len(reqs), n, self.num_parts)
         return n * 4 * (4 if pairs else 2) + len(reqs) * 8 + temp, offs, temp
 
+    def _finish_launch(self, b):
+        """After a batch's work on its stream: an asynchronous copy of the
+        device error word (no kernel, no wait), then the completion event."""
+        import torch
+        b.err_word = self.err_words.pop() if self.err_words else torch.zeros(1, dtype=torch.int32).pin_memory()
+        rs_peek_device_error_async(b.err_word, b.stream)
+        b.done_event.record(b.stream)
+
+    def _stream(self):
+        """A stream no batch in flight uses (a batch queued behind another on
+        its stream would wait for it though the device has room), else the
+        next one round robin."""
+        busy = {id(b.stream) for b in self.in_flight}
+        for k in range(len(self.streams)):
+            st = self.streams[(self.next_batch + k) % len(self.streams)]
+            if id(st) not in busy:
+                return st
+        return self.streams[self.next_batch % len(self.streams)]
+
     def _launch_direct(self, r):
         import torch
-        stream = self.streams[self.next_batch % len(self.streams)]
+        stream = self._stream()
         need = rs_sort_u32_host(None, r.vals, None, r.out_vals, r.n, self.num_parts)
         temp = self.pool.take(need)
         done = torch.cuda.Event()
         rs_sort_u32_host(r.keys, r.vals, r.out_keys, r.out_vals, r.n, self.num_parts, None, temp, stream,
                          want_offsets=False)
-        done.record(stream)
         b = _Batch(self.next_batch, [r], r.pairs, stream, None, temp, None, None, done, None)
+        self._finish_launch(b)
         r.batch = b.id
         self.next_batch += 1
         self.mem_in_use += need
@@ -229,7 +260,7 @@ class SortServer:
             return self._launch_direct(reqs[0])
         need, offs, temp_bytes = self._batch_bytes(reqs, pairs)
         n = int(offs[-1])
-        stream = self.streams[self.next_batch % len(self.streams)]
+        stream = self._stream()
         words = n * (2 if pairs else 1)
         arena = self.pool.take(2 * words * 4 + (len(reqs) + 1) * 8)
         temp = self.pool.take(max(temp_bytes, 1))
@@ -256,8 +287,8 @@ class SortServer:
                 r.out_keys.copy_(d_out[a:e], non_blocking=True)
                 if pairs:
                     r.out_vals.copy_(d_out[n + a: n + e], non_blocking=True)
-            done.record(stream)
         b = _Batch(self.next_batch, reqs, pairs, stream, arena, temp, h_off, None, done, None)
+        self._finish_launch(b)
         for r in reqs:
             r.batch = b.id
         self.next_batch += 1
@@ -267,15 +298,26 @@ class SortServer:
         self.in_flight.append(b)
 
     def _check_errors(self, b):
-        """Takes the device error word after batch b's work; on an error, marks
-        b and every batch still in flight (any of them may have raised it)."""
+        """Batch b's peek of the error word (copied after its work) is read;
+        if a bit was set, the word is taken and cleared, and b and every
+        batch still in flight (any of them may have raised it) are marked.
+        The take runs on the server's own error stream, which holds no
+        batch, so it does not wait for the batches queued after b on b's
+        stream; when the word is clear (the usual case) nothing waits."""
+        word = int(b.err_word[0]) & 0xFFFFFFFF
+        self.err_words.append(b.err_word)
+        b.err_word = None
+        if word == 0:
+            return
+        what = "RS_ERR_TIMEOUT" if word & _ERR_TIMEOUT else "RS_ERR_CUDA"
+        msg = f"{what}: device error word 0x{word:x} after the batch"
         try:
-            rs_check_device_error(b.stream)
+            rs_check_device_error(self.err_stream)
         except RsError as e:
             msg = str(e)
-            self.suspect[b.id] = msg
-            for o in self.in_flight:
-                self.suspect.setdefault(o.id, msg)
+        self.suspect[b.id] = msg
+        for o in self.in_flight:
+            self.suspect.setdefault(o.id, msg)
 
     def _assign_results(self, r) -> bool:
         """Gives r result buffers from the pool if it has none; False if the

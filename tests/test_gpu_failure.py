@@ -35,3 +35,34 @@ def test_selftest_rejects_small_temp():
     temp = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(rs.RsError):
         rs.rs_selftest_wait_timeout(temp)
+
+
+def test_peek_sees_the_word_without_clearing_it():
+    """rs_peek_device_error_async copies the word after the stream's work
+    and leaves it set; the take then reports and clears it, and a later
+    peek reads zero."""
+    import torch
+    import paper_cs_0004013_gb300 as rs
+    rs.rs_check_device_error()  # start clean
+    word = torch.full((1,), -1, dtype=torch.int32).pin_memory()
+    s = torch.cuda.current_stream()
+    rs.rs_peek_device_error_async(word, s)
+    s.synchronize()
+    assert int(word[0]) == 0
+    temp = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    rs.rs_selftest_wait_timeout(temp)
+    rs.rs_peek_device_error_async(word, s)
+    s.synchronize()
+    assert int(word[0]) & 1  # bit 0: a bounded wait gave up
+    rs.rs_peek_device_error_async(word, s)  # peeking does not clear
+    s.synchronize()
+    assert int(word[0]) & 1
+    with pytest.raises(rs.RsError) as e:
+        rs.rs_check_device_error()
+    assert e.value.status == 4
+    word[0] = -1
+    rs.rs_peek_device_error_async(word, s)
+    s.synchronize()
+    assert int(word[0]) == 0
+    with pytest.raises(ValueError):
+        rs.rs_peek_device_error_async(torch.zeros(1, dtype=torch.int32, device="cuda"), s)
