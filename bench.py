@@ -886,7 +886,9 @@ def measure_served(requests: int, rounds: int) -> dict:
     # 21.5-22.0 Gkeys/s against 19.4 with eight); results lent from a 16 GiB
     # pinned pool
     srv = SortServer(slots=16, streams=16, mem_budget=24 << 30, result_pool=ResultPool(16 << 30))
-    srv.run(make(1e9, synth.CONFIG_SEED + 5)[:100], realtime=False)  # warm-up (pools, kernels)
+    # warm-up: one whole closed-loop run, so that the device pools and the
+    # pinned result pool hold every size class the timed runs need
+    srv.run(make(1e9, synth.CONFIG_SEED + 5), realtime=False)
     points = []
     for load in (0.5, 0.8, 1.2):
         reqs = make(cap_req_s * load, synth.CONFIG_SEED + 5)
