@@ -627,7 +627,7 @@ def run_ours(args):
         del d_out, temp
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(args.steps, args.warmup)
-        extra["served"] = measure_served(args.requests, 1)
+        extra["served"] = measure_served_in_own_process(args.requests)
 
     if rank == 0:
         line = {
@@ -921,6 +921,26 @@ def measure_served(requests: int, rounds: int) -> dict:
             "serial_plain": {"value": serial_rate, "unit": "Gkeys/s", "seconds": t_serial},
             "speedup_vs_serial": (total_keys / t_closed / 1e9) / serial_rate,
             "load_points": points, "results_checked": checked["n"]}
+
+
+def measure_served_in_own_process(requests: int) -> dict:
+    """The served form measured by `bench.py --workload serve` in a process
+    of its own, as a server would run.  Inside the bench's own process, after
+    the other measurements (many pinned and device buffers held, the CPU
+    baseline's arrays), the same loop ran about a fifth slower with p99
+    latencies four times longer, and so did the serial baseline beside it."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", "serve", "--steps", "50",
+           "--requests", str(requests)]
+    res = subprocess.run(cmd, capture_output=True, text=True, cwd=ROOT)
+    lines = [l for l in res.stdout.splitlines() if l.startswith("{")]
+    if res.returncode != 0 or not lines:
+        raise SystemExit(f"served measurement failed (rc {res.returncode}): {res.stderr[-2000:]}")
+    d = json.loads(lines[-1])
+    return {"value": d["value"], "unit": d["unit"], "seconds": d["ms_per_step"] / 1e3,
+            "workload": d["config"]["workload"], "requests": requests, "total_keys": d["config"]["total_keys"],
+            "serial_plain": d["serial_plain"], "speedup_vs_serial": d["speedup_vs_serial"],
+            "load_points": d["load_points"], "results_checked": d["results_checked"],
+            "rounds": d["steps"], "process": "own (bench.py --workload serve)"}
 
 
 def run_serve(args):
