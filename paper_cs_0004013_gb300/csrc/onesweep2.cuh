@@ -50,7 +50,14 @@ struct Onesweep2Layout {
   static constexpr int TILE = THREADS * ITEMS;
   static constexpr int GKEYS = 16 * ITEMS;    // keys of one group
   static constexpr size_t KBUF = size_t(TILE) * 4;                 // staged keys
-  static constexpr size_t TBL = size_t(GROUPS) * DIGITS * 4;       // [GROUPS][DIGITS] rank words
+  // A group's row of rank words is one word longer than the digits, so that
+  // the same digit in the two halves of a warp (rows g and g + 1) falls in
+  // adjacent banks instead of one: keys with few distinct digits (clustered
+  // values, runs of equal keys) otherwise make the halves' accesses to a
+  // digit collide in its bank (2^26 keys in 8 clusters: 96 M shared-memory
+  // wavefronts per pass instead of 48 M).
+  static constexpr int ROW = DIGITS + 1;
+  static constexpr size_t TBL = size_t(GROUPS) * ROW * 4;          // [GROUPS][ROW] rank words
   // The rank words sit after the staged keys; with a payload they share
   // their space with the staged payloads, which are written only after the
   // last rank word is read.
@@ -62,6 +69,7 @@ struct Onesweep2Layout {
   static constexpr size_t SMEM = OFF_TILE + 16;
   static_assert(THREADS % 32 == 0 && THREADS >= DIGITS && THREADS <= 1024, "one thread per digit at least");
   static_assert(TILE < 65536, "positions are 16-bit");
+  static_assert(TBL % 16 == 0, "the rank words are cleared as 16-byte vectors");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -200,13 +208,14 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
   // Keys only, first executed pass of a full tile (UNSTABLE): the order of
   // keys with the same lowest digit is free (there is no earlier order to
   // keep, and keys with equal digits here are told apart by the later passes
-  // or are equal), so one shared counter per digit for the whole tile
+  // or are equal), so one shared counter per (half of a warp, digit)
   // suffices and a key's position is one atomic add on it (steps 2u and 4u
-  // below) instead of the groups' mask words.
+  // below) instead of the groups' mask words.  Two rows, one per half, keep
+  // the halves' accesses to one digit in different banks.
   constexpr bool unstable = NV == 0 && UNSTABLE;
 
-  // 2. early counts per (group, digit) [2u: per digit]
-  const uint32_t tb_grp = smem_addr(s_tbl + (unstable ? 0 : grp * DIGITS));
+  // 2. early counts per (group, digit) [2u: per (half, digit)]
+  const uint32_t tb_grp = smem_addr(s_tbl + (unstable ? (lane >> 4) : grp) * L::ROW);
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) sh_red_add(tb_grp + 4u * byte_digit(key[j], sel), 1u);
   __syncthreads();
@@ -214,25 +223,28 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
   // 3. per digit (threads 0..255): the tile's count -> aggregate status now;
   // exclusive scan over digits -> where each digit's run starts in the
   // staged tile; then each group's counter -> the position of its first key
-  // of the digit [3u: the digit's counter -> the start of its run]
+  // of the digit [3u: the two halves' counters -> where each half's keys of
+  // the digit start]
   uint32_t tot = 0, excl = 0;
   if (tid < DIGITS) {
     if constexpr (unstable) {
-      tot = s_tbl[tid];
+      tot = s_tbl[tid] + s_tbl[L::ROW + tid];
     } else {
 #pragma unroll 8
-      for (int g = 0; g < GROUPS; ++g) tot += s_tbl[g * DIGITS + tid];
+      for (int g = 0; g < GROUPS; ++g) tot += s_tbl[g * L::ROW + tid];
     }
     st_relaxed(status + size_t(tile) * DIGITS + tid, status_word<S>(parity, tile == 0, tot));
     excl = scan256_exclusive(tot, s_scan);
     if constexpr (unstable) {
+      const uint32_t c0 = s_tbl[tid];
       s_tbl[tid] = excl;
+      s_tbl[L::ROW + tid] = excl + c0;
     } else {
       uint32_t run = excl;
 #pragma unroll 8
       for (int g = 0; g < GROUPS; ++g) {
-        const uint32_t c = s_tbl[g * DIGITS + tid];
-        s_tbl[g * DIGITS + tid] = run;
+        const uint32_t c = s_tbl[g * L::ROW + tid];
+        s_tbl[g * L::ROW + tid] = run;
         run += c;
       }
     }

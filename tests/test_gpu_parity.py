@@ -127,6 +127,24 @@ def test_sort_edge_values(rs, kind):
         _pairs_check(rs, keys, plan={"digit_bits": bits})
 
 
+@pytest.mark.parametrize("kind", ["low_digit_mostly_zero", "low_digit_two_values", "runs_of_equal_keys"])
+def test_concentrated_digits_multi_launch(rs, kind):
+    """Above 2^22 keys (the pipeline of launches with the half-warp-group
+    kernel): inputs whose digits leave most lanes of a warp on one digit,
+    where the first pass's atomic ranking and the later passes' mask words
+    meet the most contention."""
+    n = (1 << 22) + 12345
+    u = synth.uniform31(n, 7)
+    hi = u & np.uint32(0xFFFFFF00)
+    keys = {
+        "low_digit_mostly_zero": hi | np.where(u % np.uint32(100) == 0, u & np.uint32(0xFF), 0).astype(np.uint32),
+        "low_digit_two_values": hi | ((u >> np.uint32(20)) & np.uint32(1)),
+        "runs_of_equal_keys": np.repeat(synth.uniform31(n // 1000 + 1, 8), 1000)[:n],
+    }[kind].astype(np.uint32)
+    _sort_check(rs, keys)
+    _pairs_check(rs, keys)
+
+
 @pytest.mark.parametrize("tile", list(range(1, 8)))
 @pytest.mark.parametrize("bits", [8, 11])
 def test_tile_shapes(rs, tile, bits):
