@@ -58,7 +58,7 @@ struct DeviceState {
   uint32_t* err = nullptr;
   uint32_t* err_taken = nullptr;
   int num_sms = 0;
-  uint32_t fused_tiles[2] = {0, 0};  // tiles the single-launch sort can hold resident (keys, pairs)
+  uint32_t fused_tiles[2][kFusedShapes] = {};  // tiles the single-launch sort holds resident ([pairs][shape])
 };
 std::mutex g_mu;
 std::mutex g_err_mu;  // one error-word check at a time (they share the copy word)
@@ -98,15 +98,17 @@ rs_status device_state(DeviceState** out) {
               "cudaFuncSetAttribute(msd)");
     int coop = 0;
     RS_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "cudaDeviceGetAttribute(coop)");
-    for (int pr = 0; pr < 2; ++pr) {
-      RS_CUDA(cudaFuncSetAttribute(fused_func(pr != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   int(fused_smem(pr != 0))),
-              "cudaFuncSetAttribute(fused)");
-      int per_sm = 0;
-      RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_func(pr != 0), 384, fused_smem(pr != 0)),
-              "cudaOccupancyMaxActiveBlocksPerMultiprocessor(fused)");
-      st.fused_tiles[pr] = coop ? uint32_t(per_sm) * uint32_t(st.num_sms) : 0u;
-    }
+    for (int pr = 0; pr < 2; ++pr)
+      for (int sh = 0; sh < kFusedShapes; ++sh) {
+        RS_CUDA(cudaFuncSetAttribute(fused_func(pr != 0, sh), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     int(fused_smem(pr != 0, sh))),
+                "cudaFuncSetAttribute(fused)");
+        int per_sm = 0;
+        RS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_func(pr != 0, sh), 384,
+                                                              fused_smem(pr != 0, sh)),
+                "cudaOccupancyMaxActiveBlocksPerMultiprocessor(fused)");
+        st.fused_tiles[pr][sh] = coop ? uint32_t(per_sm) * uint32_t(st.num_sms) : 0u;
+      }
     const SegKernels* sk = seg_kernels();
     const void* fn[10] = {sk->pass_keys[0], sk->pass_pairs[0], sk->pass_keys[1], sk->pass_pairs[1],
                           sk->tiny_keys,    sk->tiny_pairs,    sk->small_keys,   sk->small_pairs,
@@ -234,6 +236,7 @@ struct SortPlan {
   DigitSpec dig[kMaxDigits] = {};
   const OnesweepKernel* k = nullptr;
   size_t num_tiles = 0;
+  size_t status_rows = 0;  // status rows to hold when more than num_tiles (the single-launch sort's small tiles)
 };
 
 // Defaults from measurement on GB300 (uniform 31-bit keys, 2^16 .. 2^26):
@@ -354,7 +357,7 @@ Layout make_layout(const SortPlan& p, uint64_t n, bool pairs) {
   L.bases = off;
   off = align_up(off + size_t(p.nd) * digits * 4);
   L.status = off;
-  L.status_bytes = p.num_tiles * digits * (p.k->wide_status ? 8 : 4);
+  L.status_bytes = (p.status_rows > p.num_tiles ? p.status_rows : p.num_tiles) * digits * (p.k->wide_status ? 8 : 4);
   off = align_up(off + L.status_bytes);
   if (p.nd > 1 && n > 0) {
     L.alt_k = off;
@@ -701,13 +704,14 @@ rs_status run_msd(const SortPlan& p, const MsdLayout& M, const uint32_t* keys_in
 // Up to (resident blocks) x 9,216 keys with the automatic plan: clear + one
 // cooperative launch instead of clear + histogram + scans + four passes.  It
 // uses the LSD layout's control words (word 12: the barrier counter), digit
-// histograms, status rows (its tiles are larger than the 512 x 16 tiles the
-// layout is sized for) and alternate buffers.
+// histograms, status rows (the layout holds a row per tile of the smallest
+// shape up to kFusedStatusMaxKeys keys) and alternate buffers.
+constexpr uint64_t kFusedStatusMaxKeys = uint64_t(1) << 22;
 rs_status run_fused(const SortPlan& p, const Layout& L, const uint32_t* keys_in, const uint32_t* vals_in,
-                    uint32_t* keys_out, uint32_t* vals_out, uint32_t n, unsigned char* temp, DeviceState* ds,
-                    cudaStream_t s) {
+                    uint32_t* keys_out, uint32_t* vals_out, uint32_t n, int shape, unsigned char* temp,
+                    DeviceState* ds, cudaStream_t s) {
   const bool pairs = vals_in != nullptr;
-  const uint32_t tiles = (n + fused_tile_keys() - 1) / fused_tile_keys();
+  const uint32_t tiles = (n + fused_tile_keys(shape) - 1) / fused_tile_keys(shape);
   if (size_t(tiles) * 256 * 4 > L.status_bytes) return fail(RS_ERR_CUDA, "single-launch sort: status too small");
   RS_CUDA(traced(T_CLEAR, 0, s, [&] { return cudaMemsetAsync(temp, 0, L.status + size_t(tiles) * 256 * 4, s); }),
           "cudaMemsetAsync(temp)");
@@ -724,7 +728,7 @@ rs_status run_fused(const SortPlan& p, const Layout& L, const uint32_t* keys_in,
   a.status = temp + L.status;
   a.bar = reinterpret_cast<uint32_t*>(temp + L.ctrl) + 12;
   a.err = ds->err;
-  RS_CUDA(traced(T_FUSED, n, s, [&] { return launch_fused(a, tiles, pairs, s); }), "launch fused sort");
+  RS_CUDA(traced(T_FUSED, n, s, [&] { return launch_fused(a, tiles, pairs, shape, s); }), "launch fused sort");
   return RS_OK;
 }
 
@@ -740,6 +744,10 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   SortPlan p;
   st = make_plan(n, pairs, plan, &p);
   if (st != RS_OK) return st;
+  const bool automatic = plan->digit_bits == 0 && plan->mode == RS_MODE_AUTO && plan->tile == 0;
+  const bool fusable = automatic && p.R == 8 && p.nd == 4 && !p.msd && !p.k->wide_status;
+  if (fusable && n <= kFusedStatusMaxKeys)  // status rows for the single-launch sort's smallest tiles
+    p.status_rows = size_t((n + fused_tile_keys(kFusedShapes - 1) - 1) / fused_tile_keys(kFusedShapes - 1));
   Layout L = make_layout(p, n, pairs);
   MsdLayout M;
   if (p.msd) {
@@ -782,7 +790,6 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
   // sorted in shared memory by one launch (no histogram, scans or tiled
   // passes), which is several times faster for such sizes.
   const SegKernels* sk = seg_kernels();
-  const bool automatic = plan->digit_bits == 0 && plan->mode == RS_MODE_AUTO && plan->tile == 0;
   if (automatic && n <= sk->small_max) {
     LocalArgs la{};
     la.kin = keys_in;
@@ -799,12 +806,20 @@ rs_status sort_impl(const uint32_t* keys_in, const uint32_t* vals_in, uint32_t* 
     return RS_OK;
   }
   // Up to a few million keys: every tile resident at once, the whole sort in
-  // one launch (8-bit digits, the same passes).
-  if (automatic && p.R == 8 && p.nd == 4 && !p.k->wide_status &&
-      (n + fused_tile_keys() - 1) / fused_tile_keys() <= ds->fused_tiles[pairs ? 1 : 0] &&
-      size_t((n + fused_tile_keys() - 1) / fused_tile_keys()) * 1024 <= L.status_bytes)
-    return run_fused(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
-                     static_cast<unsigned char*>(temp), ds, s);
+  // one launch (8-bit digits, the same passes).  The tile shape: the smallest
+  // whose tiles still number at most one per SM, else the largest.
+  if (fusable) {
+    int sh = 0;
+    for (int c = kFusedShapes - 1; c > 0; --c)
+      if ((n + fused_tile_keys(c) - 1) / fused_tile_keys(c) <= uint64_t(ds->num_sms)) {
+        sh = c;
+        break;
+      }
+    const size_t tiles = (n + fused_tile_keys(sh) - 1) / fused_tile_keys(sh);
+    if (tiles <= ds->fused_tiles[pairs ? 1 : 0][sh] && tiles * 1024 <= L.status_bytes)
+      return run_fused(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
+                       sh, static_cast<unsigned char*>(temp), ds, s);
+  }
   return run_lsd(p, L, keys_in, pairs ? vals_in : nullptr, keys_out, pairs ? vals_out : nullptr, uint32_t(n),
                  static_cast<unsigned char*>(temp), false, ds, s);
 }

@@ -26,16 +26,24 @@
 namespace rs {
 namespace {
 
-constexpr int kFusedThreads = 384, kFusedItems = 24, kFusedMinBlocks = 2;
+constexpr int kFusedThreads = 384;
+// Tile shapes (index = fused shape): 384 x 24, 384 x 18 and 384 x 12.  A
+// pass of the single launch lasts about one tile's chain of loads, ranking,
+// lookback and write-out, so smaller tiles are faster while every tile still
+// has an SM of its own (GB300: 2^19 keys in 39.5 us with 384 x 12 against
+// 43.8 with 384 x 24) and slower once tiles share SMs (2^20 keys: 50.1
+// against 47.4).
+constexpr int kFusedItems[kFusedShapes] = {24, 18, 12};
+constexpr int fused_min_blocks(int items) { return items <= 12 ? 3 : 2; }
 // Status rows a digit thread reads per lookback round (GB300, 2^20 keys: the
 // kernel takes 48.9 us with 8 rows per round, 53.3 with 32).
 constexpr int kFusedLookback = 8;
 // Rounds of a barrier wait (about 64 ns each) before it gives up.
 constexpr uint32_t kBarrierSpinLimit = 1u << 21;
 
-template <int NV>
+template <int NV, int ITEMS>
 struct FusedLayout {
-  using L = Onesweep2Layout<kFusedThreads, kFusedItems, NV>;
+  using L = Onesweep2Layout<kFusedThreads, ITEMS, NV>;
   static constexpr size_t OFF_BASES = (L::SMEM + 15) / 16 * 16;  // [4][256]
   static constexpr size_t OFF_FLAGS = OFF_BASES + 4 * 256 * 4;   // [4] skip flags
   static constexpr size_t SMEM = OFF_FLAGS + 16;
@@ -66,9 +74,9 @@ __device__ __forceinline__ void grid_barrier(uint32_t* bar, uint32_t target, uin
   __syncthreads();
 }
 
-template <int NV>
-__global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks) fused_sort_kernel(const FusedArgs a) {
-  using FL = FusedLayout<NV>;
+template <int NV, int ITEMS>
+__global__ void __launch_bounds__(kFusedThreads, fused_min_blocks(ITEMS)) fused_sort_kernel(const FusedArgs a) {
+  using FL = FusedLayout<NV, ITEMS>;
   using L = typename FL::L;
   extern __shared__ __align__(16) unsigned char smem[];
   uint32_t* s_bases = reinterpret_cast<uint32_t*>(smem + FL::OFF_BASES);
@@ -148,27 +156,40 @@ __global__ void __launch_bounds__(kFusedThreads, kFusedMinBlocks) fused_sort_ker
     bool unstable = false;  // the first executed pass of keys on a full tile: equal digits leave in any order
     if constexpr (NV == 0) unstable = e == 0 && (size_t(tile) + 1) * L::TILE <= size_t(n);
     if (unstable)
-      onesweep2_tile<kFusedThreads, kFusedItems, NV, uint32_t, false, kFusedLookback, true, true>(job, smem);
+      onesweep2_tile<kFusedThreads, ITEMS, NV, uint32_t, false, kFusedLookback, true, true>(job, smem);
     else
-      onesweep2_tile<kFusedThreads, kFusedItems, NV, uint32_t, false, kFusedLookback, true, false>(job, smem);
+      onesweep2_tile<kFusedThreads, ITEMS, NV, uint32_t, false, kFusedLookback, true, false>(job, smem);
     if (e + 1 < m) grid_barrier(a.bar, tiles * uint32_t(2 + e), a.err);
   }
 }
 
 }  // namespace
 
-uint32_t fused_tile_keys() { return uint32_t(kFusedThreads * kFusedItems); }
-size_t fused_smem(bool pairs) { return pairs ? FusedLayout<1>::SMEM : FusedLayout<0>::SMEM; }
-const void* fused_func(bool pairs) {
-  return pairs ? reinterpret_cast<const void*>(&fused_sort_kernel<1>)
-               : reinterpret_cast<const void*>(&fused_sort_kernel<0>);
+uint32_t fused_tile_keys(int shape) { return uint32_t(kFusedThreads * kFusedItems[shape]); }
+
+template <int SH>
+struct FusedShape {
+  static constexpr int ITEMS = kFusedItems[SH];
+  static size_t smem(bool pairs) { return pairs ? FusedLayout<1, ITEMS>::SMEM : FusedLayout<0, ITEMS>::SMEM; }
+  static const void* func(bool pairs) {
+    return pairs ? reinterpret_cast<const void*>(&fused_sort_kernel<1, ITEMS>)
+                 : reinterpret_cast<const void*>(&fused_sort_kernel<0, ITEMS>);
+  }
+};
+static_assert(kFusedShapes == 3, "one FusedShape per entry of kFusedItems");
+
+size_t fused_smem(bool pairs, int shape) {
+  return shape == 0 ? FusedShape<0>::smem(pairs) : shape == 1 ? FusedShape<1>::smem(pairs) : FusedShape<2>::smem(pairs);
+}
+const void* fused_func(bool pairs, int shape) {
+  return shape == 0 ? FusedShape<0>::func(pairs) : shape == 1 ? FusedShape<1>::func(pairs) : FusedShape<2>::func(pairs);
 }
 
-cudaError_t launch_fused(const FusedArgs& a, unsigned tiles, bool pairs, cudaStream_t s) {
+cudaError_t launch_fused(const FusedArgs& a, unsigned tiles, bool pairs, int shape, cudaStream_t s) {
   FusedArgs args = a;
   void* params[] = {&args};
-  return cudaLaunchCooperativeKernel(fused_func(pairs), dim3(tiles), dim3(kFusedThreads), params, fused_smem(pairs),
-                                     s);
+  return cudaLaunchCooperativeKernel(fused_func(pairs, shape), dim3(tiles), dim3(kFusedThreads), params,
+                                     fused_smem(pairs, shape), s);
 }
 
 }  // namespace rs

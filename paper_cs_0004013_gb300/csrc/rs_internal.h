@@ -278,7 +278,7 @@ cudaError_t launch_split64(const WideArgs& a, unsigned grid, cudaStream_t s);
 cudaError_t launch_join64(const WideArgs& a, unsigned grid, cudaStream_t s);
 
 // A whole sort of up to a few million keys in one cooperative launch
-// (fused.cu): 8-bit digits, one 384 x 24 tile per block, every block resident.
+// (fused.cu): 8-bit digits, one 384 x 24, 384 x 18 or 384 x 12 tile per block, every block resident.
 struct FusedArgs {
   const uint32_t* keys_in;
   uint32_t* keys_out;
@@ -293,10 +293,11 @@ struct FusedArgs {
   uint32_t* bar;             // barrier counter, zero on entry
   uint32_t* err;             // device error word
 };
-uint32_t fused_tile_keys();
-size_t fused_smem(bool pairs);
-const void* fused_func(bool pairs);
-cudaError_t launch_fused(const FusedArgs& a, unsigned tiles, bool pairs, cudaStream_t s);
+constexpr int kFusedShapes = 3;  // tile shapes of the single-launch sort: 384 x 24, 384 x 18, 384 x 12
+uint32_t fused_tile_keys(int shape);
+size_t fused_smem(bool pairs, int shape);
+const void* fused_func(bool pairs, int shape);
+cudaError_t launch_fused(const FusedArgs& a, unsigned tiles, bool pairs, int shape, cudaStream_t s);
 
 // The MSD plan's bucketing (msd.cu): bucket = order-mapped key >> kMsdShift
 // (2^14 buckets); C chunks of ceil(n / C) keys, one block each.

@@ -10,7 +10,8 @@ from tests._gpu import to_dev, to_host_u32
 
 pytestmark = pytest.mark.gpu
 
-TILE = 384 * 24
+TILE = 384 * 24        # the large tile shape
+SMALL = 384 * 12       # the smallest tile shape (taken while its tiles number at most one per SM)
 
 
 @pytest.fixture(scope="module")
@@ -43,7 +44,8 @@ def _run(rs, keys, pairs, kind="u32"):
     return tr
 
 
-@pytest.mark.parametrize("n", [16385, 2 * TILE - 1, 2 * TILE, 2 * TILE + 1, 7 * TILE + 5, 1 << 20, (1 << 21) + 77])
+@pytest.mark.parametrize("n", [16385, 4 * SMALL - 1, 4 * SMALL, 4 * SMALL + 1, 2 * TILE - 1, 2 * TILE, 2 * TILE + 1,
+                               7 * TILE + 5, 1 << 20, (1 << 21) + 77])
 @pytest.mark.parametrize("pairs", [False, True])
 def test_sizes(rs, n, pairs):
     keys = synth.uniform31(n, n) | (synth.uniform31(n, n + 3) << np.uint32(1))
@@ -88,3 +90,21 @@ def test_large_sizes_use_the_pipeline(rs):
     n = 1 << 23
     tr = _run(rs, synth.uniform31(n, 1), False)
     assert "fused_sort" not in tr and tr.get("onesweep_r8", {}).get("launches") == 4
+
+
+@pytest.mark.parametrize("pairs", [False, True])
+def test_shape_switch_points(rs, pairs):
+    """The tile shape is the smallest whose tiles number at most one per SM
+    (384 x 12, then 384 x 18), else 384 x 24 while its tiles all fit; above
+    that the pipeline of launches runs.  Sizes on both sides of each switch,
+    derived from the SM count, with ragged last tiles."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for n in (sms * 384 * 12 - 7, sms * 384 * 12 + 1, sms * 384 * 18 - 3, sms * 384 * 18 + 1,
+              2 * sms * TILE, 2 * sms * TILE + 1):
+        keys = synth.uniform31(n, n)
+        tr = _run(rs, keys, pairs)
+        fused = tr.get("fused_sort", {}).get("launches") == 1
+        assert fused or "onesweep_r8" in tr
+        if n <= sms * TILE:
+            assert fused
