@@ -240,19 +240,21 @@ struct SortPlan {
 };
 
 // Defaults from measurement on GB300 (uniform 31-bit keys, 2^16 .. 2^26):
-// 8-bit digits beat 11-bit ones (four 512 x 24 passes take less time than
+// 8-bit digits beat 11-bit ones (four 8-bit passes take less time than
 // three 11-bit ones); LSD beats the MSD plan at every size (the MSD plan's
-// extra launches cost more than the three tiled passes it saves); the
-// 512 x 24 tile (shape 2) wins for keys above 2^22, the 512 x 16 tile
-// (shape 0) below that and for pairs (which need twice the staging memory).
+// distribution and local sorts cost more SM work than the passes it saves).
 int default_digit_bits(uint64_t /*n*/, bool /*pairs*/) { return 8; }
 uint32_t default_mode(uint64_t /*n*/, bool /*pairs*/) { return RS_MODE_LSD; }
-// Above 2^22 keys: the half-warp-group kernel at 384 x 24 for keys (GB300,
-// 2^26 keys: 233 us per pass against 260 with the lane-mask kernel at
-// 512 x 24) and the lane-mask kernel at 512 x 24 for key+payload sorts (343
-// us against 385 for the half-warp-group kernel); 512 x 16 up to 2^22 keys.
+// Tiles of the 8-bit passes (explicit LSD plans; the automatic plan sorts up
+// to a few million keys in one launch): keys take the half-warp-group kernel
+// at 384 x 24 at every size (2^20 keys: 93.5 us per sort against 95.2 for
+// the lane-mask kernel at 512 x 16; 2^22: 134 against 156; 2^26: 0.98 ms
+// against 1.12 at 512 x 24); key+payload sorts the lane-mask kernel at
+// 512 x 16 up to 2^21 keys (2^21: 120 us against 130) and at 512 x 24 above
+// (3 M keys: 139 against 147; 2^26: 343 us per pass against 385 for the
+// half-warp-group kernel, which loads the payloads after ranking).
 uint32_t default_tile(int R, bool pairs, uint64_t n) {
-  if (R == 8) return n <= (uint64_t(1) << 22) ? 1u : (pairs ? 3u : 2u);
+  if (R == 8) return pairs ? (n <= (uint64_t(1) << 21) ? 1u : 3u) : 2u;
   return pairs ? 1u : 4u;
 }
 
