@@ -205,6 +205,27 @@ def sorted_by_kind(keys: np.ndarray, key_kind: str) -> np.ndarray:
     return t ^ (np.where(top, np.uint32(0), np.uint32(f)) ^ np.uint32(m))
 
 
+def cpu_parallel_baseline(sample_keys: int = N_KEYS, reps: int = 5):
+    """The stronger CPU baseline (not the oracle): an LSD radix sort of the
+    workload's 2^26 keys on every host core (C, POSIX threads; oracle/
+    cpu_radix.c), timed over `reps` whole sorts after one untimed sort."""
+    import synth
+    from oracle import cpu_baseline as cb
+    keys = workload_keys(sample_keys, synth.CONFIG_SEED + 2, "u32")
+    out, tmp = np.empty_like(keys), np.empty_like(keys)
+    threads = cb.default_threads()
+    cb.sort(keys, threads, out, tmp)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        cb.sort(keys, threads, out, tmp)
+    el = time.perf_counter() - t0
+    if not np.array_equal(out[:: max(1, sample_keys // 4096)], np.sort(keys)[:: max(1, sample_keys // 4096)]):
+        raise SystemExit("the CPU radix baseline did not sort")
+    return {"value": reps * sample_keys / el / 1e9, "unit": "Gkeys/s", "cores": threads,
+            "host_cores": os.cpu_count(), "kind": "parallel LSD radix sort, 8-bit digits (C, POSIX threads)",
+            "sample": f"{reps} whole sorts of the workload's 2^26 keys, {el:.2f} s"}
+
+
 def cpu_baseline(sample_keys: int = N_KEYS, budget_s: float = 12.0, key_kind: str = "u32"):
     """The oracle as it stands (numpy stable sort, one core) on the
     workload itself: whole sorts of its 2^26 keys, at least two, until the
@@ -612,9 +633,11 @@ def run_ours(args):
                "api": "rs_sort_u32_host (pinned host buffers; copies of consecutive sorts overlap)",
                "link_ceiling": link}
 
-    cpu = None
+    cpu = cpu_par = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(key_kind="u64" if wide else args.key_kind)
+        if not wide and args.key_kind == "u32" and n == N_KEYS:
+            cpu_par = cpu_parallel_baseline()
 
     # Beside the headline (the plain keys-only workload at 1 GPU): the same
     # keys with a payload, the batched form (config 4) and the served form
@@ -649,6 +672,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "cpu_baseline": cpu,
+            "cpu_parallel_baseline": cpu_par,
             "e2e": e2e,
             "gpu_launches": launches,
             "kernel_ms": {k: v["total_ms"] / max(v["launches"], 1) for k, v in trace.items()},

@@ -578,3 +578,17 @@ def test_selection_with_fewer_sampled_keys_than_cells():
     assert p == 0
     _, p, _ = oracle.choose_plan(np.array([5, 5], np.uint32))  # cells 31 (rank 0) and 63 (rank 1)
     assert p == 1
+
+
+@pytest.mark.parametrize("threads", [1, 3, 16])
+def test_cpu_radix_baseline_matches_the_oracle(threads):
+    """The all-core CPU baseline (C, not the oracle) sorts like the oracle:
+    empty, tiny, ragged chunk counts, equal keys, extreme words."""
+    from oracle import cpu_baseline
+    rng = np.random.default_rng(threads)
+    cases = [np.zeros(0, np.uint32), np.array([7], np.uint32), synth.uniform31(5, 2),
+             rng.integers(0, 1 << 32, 100_003, dtype=np.uint64).astype(np.uint32),
+             synth.few_distinct(70_001, 3), np.full(50_000, 0xFFFFFFFF, np.uint32),
+             np.array([0xFFFFFFFF, 0, 0x80000000, 0x7FFFFFFF, 1] * 9000, np.uint32)]
+    for keys in cases:
+        assert np.array_equal(cpu_baseline.sort(keys, threads), oracle.sort_keys(keys))
