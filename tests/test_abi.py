@@ -161,8 +161,11 @@ def test_wide_temp_queries():
     assert r.rs_sort_u64(None, None, n, plan={"tile": 6}) >= k + 8 * n
     with pytest.raises(r.RsError):
         r.rs_sort_u64_pairs64(None, None, None, None, n, plan={"mode": 2})  # MSD is not offered for 64-bit keys
+    # against the same plan (8-bit LSD on 512 x 16 tiles, the shape with the
+    # two-payload-word kernels that the 64-bit-value sort runs)
     v64 = r.rs_sort_u32_pairs64(None, None, None, None, n)
-    assert v64 >= r.rs_sort_u32_pairs(None, None, None, None, n) + 12 * n
+    same = {"digit_bits": 8, "mode": r.RS_MODE_LSD, "tile": 1}
+    assert v64 >= r.rs_sort_u32_pairs(None, None, None, None, n, plan=same) + 12 * n
 
 
 def test_wide_entries_reject_bad_buffers_before_any_launch():
