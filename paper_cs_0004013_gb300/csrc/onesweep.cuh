@@ -368,6 +368,12 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t tile = job.tile, valid = job.valid;
 
+  // 1p. the payload words of a full tile, prefetched into L2 for step 5
+  if constexpr (NV == 1 && !PIO) {
+    if (valid == TILE && (reinterpret_cast<uintptr_t>(vin + job.base) & 15u) == 0)
+      prefetch_l2_tile(vin + job.base, uint32_t(TILE) * 4u);
+  }
+
   // 1. load the keys
   uint32_t key[ITEMS];
   const size_t wbase = job.base + size_t(warp) * 32 * ITEMS + lane;

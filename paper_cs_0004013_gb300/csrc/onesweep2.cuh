@@ -183,6 +183,12 @@ __device__ __forceinline__ void onesweep2_tile(const Tile2Job& job, unsigned cha
   (void)vout;
   (void)s_val;
 
+  // 1p. the payload words of a full tile, prefetched into L2 for step 5
+  if constexpr (NV >= 1) {
+    if (valid == TILE && (reinterpret_cast<uintptr_t>(vin + tbase) & 15u) == 0)
+      prefetch_l2_tile(vin + tbase, uint32_t(TILE) * 4u);
+  }
+
   // 1. load: group grp takes keys [grp * GKEYS, (grp + 1) * GKEYS) of the
   // tile, item j of lane l16 being key grp * GKEYS + j * 16 + l16.  Keys
   // past the end act as 0xFFFFFFFF: their digit is the largest and they

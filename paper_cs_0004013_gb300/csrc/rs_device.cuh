@@ -75,6 +75,22 @@ __device__ __forceinline__ void st_relaxed(unsigned long long* p, unsigned long 
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// ---- L2 prefetch of a tile's payloads ---------------------------------------
+// The pass kernels load a tile's payload words only after ranking its keys;
+// asking the TMA unit at the start of the tile to bring them into L2 turns
+// that load's DRAM latency into an L2 hit.  Threads 0.. of the block each
+// issue one bulk prefetch of up to kPrefetchPiece bytes (a hint: nothing to
+// wait for).  p must be 16-byte aligned and bytes a multiple of 16.
+constexpr uint32_t kPrefetchPiece = 4096;
+__device__ __forceinline__ void prefetch_l2_tile(const void* p, uint32_t bytes) {
+  const uint32_t off = threadIdx.x * kPrefetchPiece;
+  if (off < bytes) {
+    const uint32_t len = bytes - off < kPrefetchPiece ? bytes - off : kPrefetchPiece;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(static_cast<const char*>(p) + off), "r"(len)
+                 : "memory");
+  }
+}
+
 // ---- streaming global accesses for keys and payloads ----------------------
 // Keys are read once per pass: keep them out of L1.
 __device__ __forceinline__ uint32_t ld_stream(const uint32_t* p) {
