@@ -368,10 +368,16 @@ __device__ __forceinline__ void onesweep_tile(const TileJob& job, const uint32_t
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t tile = job.tile, valid = job.valid;
 
-  // 1p. the payload words of a full tile, prefetched into L2 for step 5
-  if constexpr (NV == 1 && !PIO) {
-    if (valid == TILE && (reinterpret_cast<uintptr_t>(vin + job.base) & 15u) == 0)
-      prefetch_l2_tile(vin + job.base, uint32_t(TILE) * 4u);
+  // 1p. the payload words of a full tile that step 5 reads from planes,
+  // prefetched into L2 (not those read interleaved or made from the index)
+  if constexpr (NV >= 1) {
+    if (valid == TILE && !(PIO && pio.in)) {
+      if ((reinterpret_cast<uintptr_t>(vin + job.base) & 15u) == 0) prefetch_l2_tile(vin + job.base, uint32_t(TILE) * 4u);
+      if constexpr (NV >= 2) {
+        if (vin2 && !(PIO && pio.iota) && (reinterpret_cast<uintptr_t>(vin2 + job.base) & 15u) == 0)
+          prefetch_l2_tile(vin2 + job.base, uint32_t(TILE) * 4u);
+      }
+    }
   }
 
   // 1. load the keys
