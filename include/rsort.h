@@ -69,9 +69,10 @@ typedef enum rs_status {
  *               per warp through lane-mask tables (every payload layout);
  *               2 = 384 x 24, 5 = 512 x 24, 6 = 512 x 16 and 7 = 256 x 24,
  *               ranked per half-warp with early digit counts (keys and
- *               key + uint32 payload); 4 = 1024 x 16, lane-mask tables.
+ *               key + uint32 payload); 4 = 1024 x 16 and 8 = 384 x 24,
+ *               lane-mask tables (keys and key + uint32 payload).
  *               11-bit digits: 1 to 4.  Automatic: 2 for keys; for
- *               key+payload sorts 1 up to 2^21 keys, then 3.
+ *               key+payload sorts 1 up to 2^21 keys, then 8.
  *   key_kind:   how the 32-bit key words are ordered.  RS_KEY_U32: unsigned
  *               (the paper's integers, Sec. 1.1); RS_KEY_I32: two's-complement
  *               signed; RS_KEY_F32: IEEE-754 binary32 in the totalOrder of

@@ -250,11 +250,12 @@ uint32_t default_mode(uint64_t /*n*/, bool /*pairs*/) { return RS_MODE_LSD; }
 // at 384 x 24 at every size (2^20 keys: 93.5 us per sort against 95.2 for
 // the lane-mask kernel at 512 x 16; 2^22: 134 against 156; 2^26: 0.98 ms
 // against 1.12 at 512 x 24); key+payload sorts the lane-mask kernel at
-// 512 x 16 up to 2^21 keys (2^21: 120 us against 130) and at 512 x 24 above
-// (3 M keys: 139 against 147; 2^26: 343 us per pass against 385 for the
+// 512 x 16 up to 2^21 keys (2^21: 120 us against 123 at 384 x 24 and 131 at
+// 512 x 24) and at 384 x 24, three blocks per SM, above (2^22: 159 us against
+// 172 and 174; 2^26: 322 us per pass against 332 at 512 x 24 and 362 for the
 // half-warp-group kernel, which loads the payloads after ranking).
 uint32_t default_tile(int R, bool pairs, uint64_t n) {
-  if (R == 8) return pairs ? (n <= (uint64_t(1) << 21) ? 1u : 3u) : 2u;
+  if (R == 8) return pairs ? (n <= (uint64_t(1) << 21) ? 1u : 8u) : 2u;
   return pairs ? 1u : 4u;
 }
 
@@ -1044,10 +1045,11 @@ static rs_status sort64_impl(const uint64_t* keys_in, const void* vals_in, uint6
   q.digit_bits = 8;
   q.mode = RS_MODE_LSD;
   q.key_kind = RS_KEY_U32;
-  // the shapes with interleaved-word pass kernels: 512 x 24 for keys alone
-  // above 2^22 keys (GB300, 2^26 keys: 358 against 373 us per pass), else
-  // 512 x 16 (the one with 64-bit status words and two payload words)
-  if (q.tile == 0) q.tile = (vbytes == 0 && n > (uint64_t(1) << 22) && !needs_wide_status(n)) ? 3u : 1u;
+  // the shapes with interleaved-word pass kernels: 384 x 24 (three blocks per
+  // SM) for keys alone above 2^22 keys (GB300, 2^26 keys: 335 us per pass
+  // against 349 at 512 x 24; 2^23: 20.0 against 18.7 Gkeys/s), else 512 x 16
+  // (the one with 64-bit status words and two payload words)
+  if (q.tile == 0) q.tile = (vbytes == 0 && n > (uint64_t(1) << 22) && !needs_wide_status(n)) ? 8u : 1u;
   SortPlan p;
   if (rs_status st = make_plan(n, true, &q, &p, pairs ? 2 : 1); st != RS_OK) return st;
   const Layout64 L = make_layout64(p, n, pairs, vbytes == 8);

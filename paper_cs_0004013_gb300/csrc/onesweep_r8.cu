@@ -15,7 +15,11 @@ using S64 = unsigned long long;
 //      the keys-only default above 2^22 keys;
 //   2: 512 x 24, lane-mask tables: the key+payload default above 2^22 keys;
 //   3: 1024 x 16, lane-mask tables, one block per SM;
-//   4-6: half-warp rank groups at 512 x 24, 512 x 16 and 256 x 24.
+//   4-6: half-warp rank groups at 512 x 24, 512 x 16 and 256 x 24;
+//   7: 384 x 24, lane-mask tables, three blocks per SM: the key+payload
+//      default above 2^21 keys (2^26: 322 us per pass against 332 at 512 x 24)
+//      and, with interleaved words, the 64-bit keys default above 2^22 keys
+//      (335 against 349 us); with two payload words it spills and gains nothing.
 // GB300, 2^26 uniform 31-bit keys, per pass: shape 1 233 us (keys), shape 2
 // 260 us (keys) and 343 us (key+payload), shape 4 238 / 385 us.
 static const OnesweepKernel kR8[] = {
@@ -36,6 +40,8 @@ static const OnesweepKernel kR8[] = {
     make_onesweep2<512, 24, 0, S64, 2>(4), make_onesweep2<512, 24, 1, S64, 2>(4),
     make_onesweep2<512, 16, 0, S32, 2>(5), make_onesweep2<512, 16, 1, S32, 2>(5),
     make_onesweep2<256, 24, 0, S32, 4>(6), make_onesweep2<256, 24, 1, S32, 4>(6),
+    make_onesweep<8, 384, 24, false, S32, 3, false>(7), make_onesweep<8, 384, 24, true, S32, 3, false>(7),
+    make_onesweep<8, 384, 24, true, S32, 3, false, true>(7),  // interleaved: 64-bit keys
 };
 
 const OnesweepKernel* onesweep_kernels_r8(int* count) {

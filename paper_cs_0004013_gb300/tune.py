@@ -47,7 +47,7 @@ def candidate_plans(n: int, pairs: bool) -> list[dict]:
     shapes (lane-mask and half-warp-group kernels), 11-bit LSD over its
     large tiles, and the MSD plan where its buckets can fit the local sort."""
     out = [{"digit_bits": 0, "mode": RS_MODE_AUTO, "tile": 0}]
-    out += [{"digit_bits": 8, "mode": RS_MODE_LSD, "tile": t} for t in (1, 2, 3, 5, 6, 7)]
+    out += [{"digit_bits": 8, "mode": RS_MODE_LSD, "tile": t} for t in (1, 2, 3, 5, 6, 7, 8)]
     out += [{"digit_bits": 11, "mode": RS_MODE_LSD, "tile": t} for t in (2, 4)]
     if n < (1 << 30) - (1 << 16):
         out.append({"digit_bits": 8, "mode": RS_MODE_MSD, "tile": 0})

@@ -58,7 +58,7 @@ def test_skipped_digits(rs, kind):
     _check(rs, np.full(n, 0xBFF0000000000000, np.uint64), kind)  # every digit skipped: a copy
 
 
-@pytest.mark.parametrize("tile", list(range(1, 8)))
+@pytest.mark.parametrize("tile", list(range(1, 9)))
 def test_tile_shapes(rs, tile):
     plan = {"tile": tile}
     try:

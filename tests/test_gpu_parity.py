@@ -145,7 +145,7 @@ def test_concentrated_digits_multi_launch(rs, kind):
     _pairs_check(rs, keys)
 
 
-@pytest.mark.parametrize("tile", list(range(1, 8)))
+@pytest.mark.parametrize("tile", list(range(1, 9)))
 @pytest.mark.parametrize("bits", [8, 11])
 def test_tile_shapes(rs, tile, bits):
     """Every registered tile shape (plain and persistent pipelined kernels),
