@@ -48,8 +48,13 @@ WORKLOAD = "plain sort of 2^26 uint32 keys uniform in [0, 2^31-1], keys only, 64
 KEY_KINDS = {"u32": 0, "i32": 1, "f32": 2}
 
 
+def size_text(n: int) -> str:
+    """n as a power of two when it is one."""
+    return f"2^{n.bit_length() - 1}" if n > 0 and n & (n - 1) == 0 else str(n)
+
+
 def workload_label(n: int, pairs: bool, key_kind: str = "u32") -> str:
-    size = f"2^{n.bit_length() - 1}" if n & (n - 1) == 0 else str(n)
+    size = size_text(n)
     w = WORKLOAD.replace("2^26", size)
     if key_kind == "i32":
         w = w.replace("uint32 keys uniform in [0, 2^31-1]", "int32 keys uniform over all 2^32 values")
@@ -255,15 +260,17 @@ def run_reference(args):
         return 0
     import oracle
     import synth
-    keys = synth.uniform31(N_KEYS, synth.CONFIG_SEED + 2)  # the workload itself
+    total = args.n  # the workload's keys (2^26 by default)
+    keys = synth.uniform31(total, synth.CONFIG_SEED + 2)  # the workload itself
     # Each step sorts a prefix of the workload's keys, as long as the whole
     # run fits REFERENCE_BUDGET_S (the oracle takes seconds per 2^26 keys):
     # the prefix is the longest power of two whose estimated time, scaled
-    # from one timed sort of 2^20 keys, fits the steps plus one warm-up.
+    # from one timed sort of up to 2^20 keys, fits the steps plus one warm-up.
+    probe = min(total, 1 << 20)
     t0 = time.perf_counter()
-    oracle.sort_keys(keys[: 1 << 20])
-    per_key = (time.perf_counter() - t0) / (1 << 20) * 1.3  # n log n growth up to 2^26
-    size = N_KEYS
+    oracle.sort_keys(keys[:probe])
+    per_key = (time.perf_counter() - t0) / max(probe, 1) * 1.3  # n log n growth up to 2^26
+    size = total
     while size > (1 << 20) and (args.steps + min(args.warmup, 1)) * size * per_key > REFERENCE_BUDGET_S:
         size //= 2
     sample = keys[:size]
@@ -279,12 +286,12 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "Gkeys/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "keys_per_step": int(sample.size)},
+            "data": "synthetic", "config": {"workload": workload_label(total, False), "keys_per_step": int(sample.size)},
             "cpu_baseline": {"value": rate, "unit": "Gkeys/s", "cores": 1, "host_cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": f"each step sorts the first 2^{size.bit_length() - 1} of the workload's "
-                                       "2^26 uniform 31-bit keys (numpy stable sort, one host thread); "
-                                       "at most one warm-up sort"},
+                             "sample": f"each step sorts the first {size_text(sample.size)} of the workload's "
+                                       f"{size_text(total)} uniform 31-bit keys (numpy stable sort, one host "
+                                       "thread); at most one warm-up sort"},
             "e2e": {"value": rate, "unit": "Gkeys/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
