@@ -774,7 +774,7 @@ def measure_batched(steps: int, warmup: int) -> dict:
     tuner = tune.Tuner(cache_path=os.path.join(tempfile.mkdtemp(), "plans.json"), reps=2)
     tuned = tuner.best_segmented_plan(offs, pairs=True, keys=dk, vals=dv)
     tuner.install()
-    default_plan = {"digit_bits": 8, "mode": 0, "tile": 2}
+    default_plan = {"digit_bits": 8, "mode": 0, "tile": 3}  # the compiled default
     temp = torch.empty(max(temp.numel(), rs.rs_sort_u32_segmented(None, dv, None, vo, None, offs, S, n, 64)),
                        dtype=torch.uint8, device="cuda")
 

@@ -119,13 +119,14 @@ rs_status rs_sort_u32_pairs(const uint32_t* keys_in, const uint32_t* vals_in,
  * partition offsets made absolute by adding the segment start.
  * h_seg_offsets is a HOST copy of the same offsets, used to plan the
  * launches (segment classes by size) without reading device memory.
- * plan: digit_bits 0 or 8; tile 1 (512 x 16 tiled passes) or 2 (512 x 24
- * for keys, 512 x 22 with payloads); mode MSD or automatic (every segment
+ * plan: digit_bits 0 or 8; tile 1 (512 x 16 tiled passes), 2 (512 x 24
+ * for keys, 512 x 22 with payloads) or 3 (384 x 20, three blocks per SM);
+ * mode MSD or automatic (every segment
  * of up to 16,384 keys is sorted by one block in shared memory, larger ones
  * by tiled passes) or LSD (only segments of up to 4,096 keys go to the
  * one-block sort); key_kind as for rs_sort_u32.  Zero fields take the plan
  * installed for the batch's size class (rs_set_default_plan), else the
- * compiled defaults (tile 2, automatic).                                    */
+ * compiled defaults (tile 3, automatic).                                    */
 rs_status rs_sort_u32_segmented(const uint32_t* keys_in, const uint32_t* vals_in,
                                 uint32_t* keys_out, uint32_t* vals_out,
                                 const uint64_t* d_seg_offsets,
@@ -339,8 +340,9 @@ enum {
  * use) hands its choices of digit width, tile shape and MSD or LSD to the
  * library; the paper chose its algorithm per data set by measurement too
  * (Sec. 4.2).  Host-only; thread-safe.  For rs_sort_u32_segmented, tile is
- * 1 (512 x 16 tiled passes) or 2 (512 x 24 for keys, 512 x 22 with
- * payloads, the default) and mode LSD sends only segments of up to 4,096
+ * 1 (512 x 16 tiled passes), 2 (512 x 24 for keys, 512 x 22 with
+ * payloads) or 3 (384 x 20, the default) and mode LSD sends only segments
+ * of up to 4,096
  * keys to the one-block sort, MSD or automatic every segment up to 16,384. */
 rs_status rs_set_default_plan(uint32_t entry, uint32_t size_class, const rs_plan* plan);
 

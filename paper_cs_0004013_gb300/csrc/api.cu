@@ -110,14 +110,14 @@ rs_status device_state(DeviceState** out) {
         st.fused_tiles[pr][sh] = coop ? uint32_t(per_sm) * uint32_t(st.num_sms) : 0u;
       }
     const SegKernels* sk = seg_kernels();
-    const void* fn[10] = {sk->pass_keys[0], sk->pass_pairs[0], sk->pass_keys[1], sk->pass_pairs[1],
-                          sk->tiny_keys,    sk->tiny_pairs,    sk->small_keys,   sk->small_pairs,
-                          sk->hist,         sk->hist_xf};
-    const size_t sm[10] = {sk->pass_smem_keys[0], sk->pass_smem_pairs[0], sk->pass_smem_keys[1],
-                           sk->pass_smem_pairs[1], sk->tiny_smem_keys,     sk->tiny_smem_pairs,
-                           sk->small_smem_keys,    sk->small_smem_pairs,   sk->hist_smem,
-                           sk->hist_smem};
-    for (int i = 0; i < 10; ++i)
+    const void* fn[12] = {sk->pass_keys[0], sk->pass_pairs[0], sk->pass_keys[1], sk->pass_pairs[1],
+                          sk->pass_keys[2], sk->pass_pairs[2], sk->tiny_keys,    sk->tiny_pairs,
+                          sk->small_keys,   sk->small_pairs,   sk->hist,         sk->hist_xf};
+    const size_t sm[12] = {sk->pass_smem_keys[0], sk->pass_smem_pairs[0], sk->pass_smem_keys[1],
+                           sk->pass_smem_pairs[1], sk->pass_smem_keys[2],  sk->pass_smem_pairs[2],
+                           sk->tiny_smem_keys,     sk->tiny_smem_pairs,    sk->small_smem_keys,
+                           sk->small_smem_pairs,   sk->hist_smem,          sk->hist_smem};
+    for (int i = 0; i < 12; ++i)
       RS_CUDA(cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm[i])),
               "cudaFuncSetAttribute(segmented)");
     st.ready = true;
@@ -473,7 +473,7 @@ struct SegLayout {
 };
 
 // Shape of the segmented pipeline's tiled passes when a plan names none.
-constexpr int kSegDefaultShape = 1;
+constexpr int kSegDefaultShape = 2;  // 384 x 20 tiles, three blocks per SM
 
 SegLayout make_seg_layout(size_t off, uint32_t num_segs, uint64_t total_n, int nd, bool pairs,
                           int shape = kSegDefaultShape) {
@@ -583,7 +583,10 @@ rs_status run_segmented(const SegLayout& L, unsigned char* temp, const uint32_t*
     ga.xin = p == 0 ? xin : kIdentityXform;
     ga.xout = p == nd - 1 ? xout : kIdentityXform;
     RS_CUDA(traced(T_SEGPASS, 0, s,
-                   [&] { return launch_seg_pass(ga, pairs, L.shape, cap(L.tiles_ub, size_t(sms) * 2), s); }),
+                   [&] {
+                     return launch_seg_pass(ga, pairs, L.shape,
+                                            cap(L.tiles_ub, size_t(sms) * sk->blocks_per_sm[L.shape]), s);
+                   }),
             "launch seg_pass");
     src_k = ga.kout;
     src_v = ga.vout;

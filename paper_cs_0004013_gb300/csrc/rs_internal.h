@@ -230,10 +230,11 @@ struct LocalArgs {
 };
 
 // Tiled-pass shapes of the segmented pipeline (rs_plan.tile = shape + 1).
-constexpr int kSegShapes = 2;
+constexpr int kSegShapes = 3;
 
 struct SegKernels {
   uint32_t tile_keys[kSegShapes], tile_pairs[kSegShapes], tiny_max, small_max;
+  uint32_t blocks_per_sm[kSegShapes];  // the persistent pass's resident blocks
   uint32_t tile(bool pairs, int shape) const { return pairs ? tile_pairs[shape] : tile_keys[shape]; }
   size_t pass_smem_keys[kSegShapes], pass_smem_pairs[kSegShapes];
   size_t tiny_smem_keys, tiny_smem_pairs, small_smem_keys, small_smem_pairs;

@@ -340,9 +340,12 @@ cudaError_t launch_local(const LocalArgs& a, unsigned grid, cudaStream_t s) {
 }  // namespace
 
 // Tiled passes over large segments, 8-bit digits.  Shape 0: 512 x 16 tiles
-// (keys and key+payload); shape 1 (the default): 512 x 24 for keys, 512 x 22
-// for key+payload.
+// (keys and key+payload); shape 1: 512 x 24 for keys, 512 x 22 for
+// key+payload; shape 2 (the default): 384 x 20 for both, three blocks per SM
+// (the batch of 1774 key+payload arrays: 47.7 Gkeys/s against 47.0; 384 x 24
+// spills in the persistent loop and takes 39.6).
 constexpr int kSegThreads = 512, kSegItemsKeys = 24, kSegItemsPairs = 22, kSegItemsSmall = 16;
+constexpr int kSegThreads3 = 384, kSegItems3 = 20;
 // Local sorts: tiny segments <= 256 x 16 keys, small ones <= 1024 x 16 keys.
 constexpr int kTinyThreads = 256, kSmallThreads = 1024, kLocalItems = 16;
 // Segment histograms: one 1024-thread block per SM (lane copies of up to
@@ -351,20 +354,27 @@ constexpr int kSegHistThreads = 1024;
 
 const SegKernels* seg_kernels() {
   static const SegKernels k = {
-      {uint32_t(kSegThreads * kSegItemsSmall), uint32_t(kSegThreads * kSegItemsKeys)},
-      {uint32_t(kSegThreads * kSegItemsSmall), uint32_t(kSegThreads * kSegItemsPairs)},
+      {uint32_t(kSegThreads * kSegItemsSmall), uint32_t(kSegThreads * kSegItemsKeys),
+       uint32_t(kSegThreads3 * kSegItems3)},
+      {uint32_t(kSegThreads * kSegItemsSmall), uint32_t(kSegThreads * kSegItemsPairs),
+       uint32_t(kSegThreads3 * kSegItems3)},
       uint32_t(kTinyThreads * kLocalItems),
       uint32_t(kSmallThreads * kLocalItems),
-      {OnesweepLayout<8, kSegThreads, kSegItemsSmall, 0>::SMEM, OnesweepLayout<8, kSegThreads, kSegItemsKeys, 0>::SMEM},
-      {OnesweepLayout<8, kSegThreads, kSegItemsSmall, 1>::SMEM, OnesweepLayout<8, kSegThreads, kSegItemsPairs, 1>::SMEM},
+      {2u, 2u, 3u},
+      {OnesweepLayout<8, kSegThreads, kSegItemsSmall, 0>::SMEM, OnesweepLayout<8, kSegThreads, kSegItemsKeys, 0>::SMEM,
+       OnesweepLayout<8, kSegThreads3, kSegItems3, 0>::SMEM},
+      {OnesweepLayout<8, kSegThreads, kSegItemsSmall, 1>::SMEM, OnesweepLayout<8, kSegThreads, kSegItemsPairs, 1>::SMEM,
+       OnesweepLayout<8, kSegThreads3, kSegItems3, 1>::SMEM},
       LocalLayout<kTinyThreads, kLocalItems, false>::SMEM,
       LocalLayout<kTinyThreads, kLocalItems, true>::SMEM,
       LocalLayout<kSmallThreads, kLocalItems, false>::SMEM,
       LocalLayout<kSmallThreads, kLocalItems, true>::SMEM,
       {reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsSmall, false, 2>),
-       reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsKeys, false, 2>)},
+       reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsKeys, false, 2>),
+       reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads3, kSegItems3, false, 3>)},
       {reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsSmall, true, 2>),
-       reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsPairs, true, 2>)},
+       reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads, kSegItemsPairs, true, 2>),
+       reinterpret_cast<const void*>(&seg_pass_kernel<kSegThreads3, kSegItems3, true, 3>)},
       reinterpret_cast<const void*>(&local_sort_kernel<kTinyThreads, kLocalItems, false>),
       reinterpret_cast<const void*>(&local_sort_kernel<kTinyThreads, kLocalItems, true>),
       reinterpret_cast<const void*>(&local_sort_kernel<kSmallThreads, kLocalItems, false>),
@@ -394,6 +404,9 @@ cudaError_t launch_seg_scan(const SegScanArgs& a, unsigned grid, cudaStream_t s)
   return cudaGetLastError();
 }
 cudaError_t launch_seg_pass(const SegPassArgs& a, bool pairs, int shape, unsigned grid, cudaStream_t s) {
+  if (shape == 2)
+    return pairs ? launch_seg_pass<kSegThreads3, kSegItems3, true, 3>(a, grid, s)
+                 : launch_seg_pass<kSegThreads3, kSegItems3, false, 3>(a, grid, s);
   if (shape == 0)
     return pairs ? launch_seg_pass<kSegThreads, kSegItemsSmall, true, 2>(a, grid, s)
                  : launch_seg_pass<kSegThreads, kSegItemsSmall, false, 2>(a, grid, s);

@@ -55,11 +55,11 @@ def candidate_plans(n: int, pairs: bool) -> list[dict]:
 
 
 def segmented_candidates(pairs: bool) -> list[dict]:
-    """Plans of the segmented sort: its two tiled-pass shapes, each with the
+    """Plans of the segmented sort: its three tiled-pass shapes, each with the
     one-block local sort for every segment that fits (MSD: bucket, then
     local sort) or only for the smallest class (LSD: tiled passes above
     4,096 keys)."""
-    return [{"digit_bits": 8, "mode": m, "tile": t} for t in (1, 2) for m in (RS_MODE_MSD, RS_MODE_LSD)]
+    return [{"digit_bits": 8, "mode": m, "tile": t} for t in (1, 2, 3) for m in (RS_MODE_MSD, RS_MODE_LSD)]
 
 
 def _default_cache() -> str:

@@ -95,7 +95,7 @@ def test_installed_segmented_plan_is_the_one_that_runs(rs, pairs):
 
 
 @pytest.mark.parametrize("plan", [{"tile": 1, "mode": 1}, {"tile": 1, "mode": 2}, {"tile": 2, "mode": 1},
-                                  {"tile": 2, "mode": 2}])
+                                  {"tile": 2, "mode": 2}, {"tile": 3, "mode": 1}, {"tile": 3, "mode": 2}])
 def test_every_segmented_candidate_matches_the_oracle(rs, plan):
     import torch
     offs = np.concatenate([[0], np.cumsum([0, 1, 4095, 4097, 16384, 16385, 30000, 3, 70000])]).astype(np.uint64)

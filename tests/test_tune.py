@@ -43,8 +43,8 @@ def test_picks_fastest_and_caches(tmp_path, monkeypatch):
 
 def test_segmented_candidates_cover_shapes_and_modes():
     c = tune.segmented_candidates(pairs=True)
-    assert {(p["tile"], p["mode"]) for p in c} == {(1, tune.RS_MODE_MSD), (1, tune.RS_MODE_LSD),
-                                                   (2, tune.RS_MODE_MSD), (2, tune.RS_MODE_LSD)}
+    assert {(p["tile"], p["mode"]) for p in c} == {(t, m) for t in (1, 2, 3)
+                                                   for m in (tune.RS_MODE_MSD, tune.RS_MODE_LSD)}
 
 
 def test_segmented_pick_uses_mean_segment_size_class(tmp_path, monkeypatch):
