@@ -35,8 +35,9 @@ constexpr int kFusedThreads = 384;
 // against 47.4).
 constexpr int kFusedItems[kFusedShapes] = {24, 18, 12};
 constexpr int fused_min_blocks(int items) { return items <= 12 ? 3 : 2; }
-// Status rows a digit thread reads per lookback round (GB300, 2^20 keys: the
-// kernel takes 48.9 us with 8 rows per round, 53.3 with 32).
+// Status rows a digit thread reads per lookback round (GB300, 2^20 keys in
+// 152 tiles of 384 x 18: the kernel takes 44.7 us with 8 rows per round,
+// 47.8 with 16 and 62.1 with 32).
 constexpr int kFusedLookback = 8;
 // Rounds of a barrier wait (about 64 ns each) before it gives up.
 constexpr uint32_t kBarrierSpinLimit = 1u << 21;
